@@ -1,0 +1,173 @@
+/*
+ * pb.h -- C ABI of the GB300 (sm_103a) exact butterfly-counting library.
+ *
+ * Implements the counting framework of Shi & Shun, "Parallel Algorithms for
+ * Butterfly Computations": rank the vertices (Sec. "Ranking"), retrieve the
+ * wedges whose centre and second endpoint rank above the first endpoint
+ * (Algorithm 2), aggregate them by endpoint pair (Sec. "Wedge aggregation"),
+ * and turn the group sizes d into global, per-vertex (Algorithm 3, Eq. 1) and
+ * per-edge (Algorithm 4, Eq. 2) butterfly counts with atomic adds
+ * (Sec. "Butterfly aggregation").  All counts are exact uint64.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a pb_status and never aborts the process; on failure
+ *    pb_last_error() gives a message (thread-local, valid until the next call
+ *    on the same thread).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call enqueues its device work on that stream and returns
+ *    after the stream has completed it, so outputs are ready on return.
+ *  - Pointers marked "host or device" are device pointers when the matching
+ *    on_device / out_on_device flag is non-zero, else host pointers.  Callers
+ *    own their inputs and outputs; the library copies inputs and owns the
+ *    graph and all scratch memory, which pb_graph_free releases.
+ *  - A pb_graph is bound to the device that was current when it was created;
+ *    calls on it make that device current.  Calls on one graph must not run
+ *    concurrently; distinct graphs may be used from different threads.
+ *  - Vertex ids are per side: u in [0, nU), v in [0, nV).  Internally vertex
+ *    x has a "global id" (u, or nU + v) and, after ranking, a rank in [0, n).
+ *  - Limits: nU + nV < 2^31 and at most 2^31 - 1 distinct edges.
+ */
+#ifndef PB_H
+#define PB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pb_graph pb_graph; /* opaque, library-owned */
+
+/* Ranking functions f of Sec. "Ranking" (PREPROCESS, Algorithm 1 sorts the
+ * vertices by f; rank 0 comes first and is the first endpoint x1 of the
+ * wedges it retrieves).
+ *  SIDE:          every vertex of one side before the other; the side placed
+ *                 first is the one whose vertices, as endpoints, give fewer
+ *                 wedges (ties: U); ids in order within a side.
+ *  DEGREE:        decreasing degree (Chiba-Nishizeki); ties by global id.
+ *  APPROX_DEGREE: decreasing floor(log2 degree); ties keep global-id order;
+ *                 degree-0 vertices last. */
+typedef enum {
+  PB_RANK_SIDE = 0,
+  PB_RANK_DEGREE = 1,
+  PB_RANK_APPROX_DEGREE = 2
+} pb_rank_kind;
+
+/* Wedge aggregation methods of Sec. "Wedge aggregation".
+ *  SORT:  wedge keys (x1, x2) are materialised chunk by chunk (the paper's
+ *         limit on wedges held in memory), radix-sorted on the device and
+ *         grouped; group sizes are d(x1, x2).
+ *  HASH:  open-addressing hash tables keyed by the second endpoint, one per
+ *         first endpoint: in shared memory for first endpoints with few
+ *         wedges, in device memory (atomic-add combining) for heavy ones.
+ *  HIST:  as HASH for light first endpoints; heavy (low-rank) first endpoints
+ *         count their wedges in a dense histogram over all second endpoints,
+ *         shared by a thread-block cluster.
+ *  BATCH: dense arrays over all second endpoints, one per concurrently
+ *         processed first endpoint, as many as the scratch budget holds
+ *         (simple batching); first endpoints are taken in decreasing order of
+ *         wedge count (wedge-aware).  First endpoints with few wedges use
+ *         shared-memory tables.
+ *  AUTO:  chosen per graph from degree and wedge statistics. */
+typedef enum {
+  PB_AGG_SORT = 0,
+  PB_AGG_HASH = 1,
+  PB_AGG_HIST = 2,
+  PB_AGG_BATCH = 3,
+  PB_AGG_AUTO = 4
+} pb_agg;
+
+typedef enum {
+  PB_OK = 0,
+  PB_ERR_INVALID = 1,  /* bad argument, id out of range, size over a limit */
+  PB_ERR_NOMEM = 2,    /* device or host allocation failed */
+  PB_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  PB_ERR_SCRATCH = 4,  /* scratch budget too small for one unit of work */
+  PB_ERR_TIMEOUT = 5,  /* a bounded device wait ran out */
+  PB_ERR_OVERFLOW = 6  /* a count does not fit in uint64 */
+} pb_status;
+
+/* Graph statistics (filled by pb_graph_info). */
+typedef struct {
+  uint32_t nU, nV;
+  uint64_t m_in;       /* edges given, duplicates included */
+  uint64_t m;          /* distinct edges */
+  uint32_t max_deg_U, max_deg_V;
+  int32_t rank_kind;   /* pb_rank_kind, 3 = custom ranking, -1 = not ranked */
+  uint64_t W;          /* wedges retrieved under the current ranking */
+  uint64_t max_wedges_x1; /* largest wedge count of a single first endpoint */
+  uint64_t device_bytes;  /* device memory held by the graph (scratch included) */
+} pb_graph_info_t;
+
+/* Builds a graph from m edge pairs (u[k], v[k]) (preliminaries: bipartite CSR;
+ * Sec. "Experiments / Environment": duplicate edges removed).  u and v are
+ * host or device arrays of m uint32 each (on_device selects).  Duplicated
+ * pairs collapse into one edge; per-edge outputs still have one entry per
+ * input pair, in input order.  Returns PB_ERR_INVALID if u[k] >= nU or
+ * v[k] >= nV for any k.  The graph is ranked with PB_RANK_SIDE until pb_rank
+ * is called.  *out receives the handle (NULL on failure). */
+pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u,
+                              const uint32_t *v, int on_device, void *stream,
+                              pb_graph **out);
+
+/* PREPROCESS (Algorithm 1): ranks the vertices with f = kind, renames them to
+ * their ranks, sorts every adjacency list by decreasing rank and stores, for
+ * every adjacency entry (x, y), deg_x(y) = |N_x(y)| (the number of y's
+ * neighbours ranked above x), plus the wedge count of every first endpoint
+ * and their prefix sum (the work split of Algorithm 2). */
+pb_status pb_rank(pb_graph *g, pb_rank_kind kind, void *stream);
+
+/* As pb_rank with an explicit ranking: rank_of[x] for global id x (U ids
+ * then V ids), a permutation of [0, nU + nV) (host or device, on_device
+ * selects).  PB_ERR_INVALID if it is not a permutation.  Counts do not depend
+ * on the ranking (Sec. "Preprocessing"); only the retrieved wedges do. */
+pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, void *stream);
+
+/* Writes rank_of[x] for every global id x (host or device). */
+pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream);
+
+/* Total butterfly count: sum over endpoint pairs of C(d, 2) (footnote of
+ * Sec. "Butterfly aggregation").  *out is a host uint64.
+ * scratch_bytes bounds the aggregation scratch (0 = library default, 16 GiB
+ * or less); work is chunked to fit, PB_ERR_SCRATCH if one first endpoint
+ * cannot fit alone. */
+pb_status pb_count_global(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out,
+                          void *stream);
+
+/* Per-vertex counts (Algorithm 3 / Eq. 1): out_U[nU] and out_V[nV], uint64,
+ * host or device (out_on_device selects); either may be NULL. */
+pb_status pb_count_vertex(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out_U,
+                          uint64_t *out_V, int out_on_device, void *stream);
+
+/* Per-edge counts (Algorithm 4 / Eq. 2): out_E[m_in], uint64, one entry per
+ * input pair in input order (duplicates repeat their edge's count). */
+pb_status pb_count_edge(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out_E,
+                        int out_on_device, void *stream);
+
+/* All three in one wedge pass: any output may be NULL.  out_global is a host
+ * uint64; out_U, out_V, out_E follow out_on_device. */
+pb_status pb_count_all(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out_global,
+                       uint64_t *out_U, uint64_t *out_V, uint64_t *out_E, int out_on_device,
+                       void *stream);
+
+/* Number of wedges Algorithm 2 retrieves under the current ranking. */
+pb_status pb_wedge_count(const pb_graph *g, uint64_t *W);
+
+/* Statistics of the graph (host struct). */
+pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info);
+
+/* Releases the graph and every device buffer it holds.  NULL is accepted. */
+pb_status pb_graph_free(pb_graph *g);
+
+/* Number of device kernels the library has launched in this process (all
+ * graphs, all devices); used to report launch counts. */
+uint64_t pb_kernel_launches(void);
+
+const char *pb_last_error(void);
+const char *pb_status_string(pb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PB_H */

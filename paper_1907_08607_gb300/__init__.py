@@ -1,0 +1,243 @@
+"""Python binding of the GB300 exact butterfly-counting library (libpb.so).
+
+Argument marshalling only: every step of the counting path runs in the CUDA
+kernels behind the C ABI of ``include/pb.h``.  PyTorch supplies device memory
+and the current CUDA stream.  There is no CPU fallback: if ``libpb.so`` has
+not been built (``paper_1907_08607_gb300.build.build()``) or no CUDA device is
+present, calls raise.
+
+Names follow the paper (Shi & Shun, "Parallel Algorithms for Butterfly
+Computations"): ranking ``side`` / ``degree`` / ``approx_degree`` (Sec.
+"Ranking"), wedge aggregation ``sort`` / ``hash`` / ``hist`` / ``batch``
+(Sec. "Wedge aggregation"), global / per-vertex / per-edge counts
+(Algorithms 3 and 4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpb.so")
+
+RANKS = {"side": 0, "degree": 1, "approx_degree": 2}
+AGGS = {"sort": 0, "hash": 1, "hist": 2, "batch": 3, "auto": 4}
+STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 4: "PB_ERR_SCRATCH",
+          5: "PB_ERR_TIMEOUT", 6: "PB_ERR_OVERFLOW"}
+
+# Every function the C ABI exports (include/pb.h).
+ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ranks", "pb_count_global",
+               "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
+               "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("nU", ctypes.c_uint32), ("nV", ctypes.c_uint32), ("m_in", ctypes.c_uint64),
+                ("m", ctypes.c_uint64), ("max_deg_U", ctypes.c_uint32), ("max_deg_V", ctypes.c_uint32),
+                ("rank_kind", ctypes.c_int32), ("W", ctypes.c_uint64), ("max_wedges_x1", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpb.so and declare the C signatures (no compute)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libpb.so not built at {path}; run paper_1907_08607_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        lib.pb_graph_from_edges.argtypes = [u32, u32, u64, vp, vp, i32, vp, ctypes.POINTER(vp)]
+        lib.pb_rank.argtypes = [vp, i32, vp]
+        lib.pb_rank_custom.argtypes = [vp, vp, i32, vp]
+        lib.pb_graph_ranks.argtypes = [vp, vp, i32, vp]
+        lib.pb_count_global.argtypes = [vp, i32, u64, u64p, vp]
+        lib.pb_count_vertex.argtypes = [vp, i32, u64, vp, vp, i32, vp]
+        lib.pb_count_edge.argtypes = [vp, i32, u64, vp, i32, vp]
+        lib.pb_count_all.argtypes = [vp, i32, u64, u64p, vp, vp, vp, i32, vp]
+        lib.pb_wedge_count.argtypes = [vp, u64p]
+        lib.pb_graph_info.argtypes = [vp, ctypes.POINTER(GraphInfo)]
+        lib.pb_graph_free.argtypes = [vp]
+        for f in ("pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ranks", "pb_count_global",
+                  "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
+                  "pb_graph_free"):
+            getattr(lib, f).restype = i32
+        lib.pb_kernel_launches.argtypes = []
+        lib.pb_kernel_launches.restype = ctypes.c_uint64
+        lib.pb_last_error.argtypes = []
+        lib.pb_last_error.restype = ctypes.c_char_p
+        lib.pb_status_string.argtypes = [i32]
+        lib.pb_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = _lib.pb_last_error().decode(errors="replace") if _lib else ""
+        raise PBError(rc, msg)
+
+
+def kernel_launches() -> int:
+    return int(load_library().pb_kernel_launches())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the butterfly library runs on the GPU only")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _edge_arg(x, torch):
+    """(pointer, on_device, keepalive) for a uint32 edge array (torch or numpy)."""
+    if isinstance(x, torch.Tensor):
+        if x.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("edge tensors must be int32/uint32")
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.ascontiguousarray(x, dtype=np.uint32)
+    return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+@dataclass
+class Counts:
+    global_count: int | None
+    per_vertex_U: object | None
+    per_vertex_V: object | None
+    per_edge: object | None
+
+
+class Graph:
+    """A bipartite graph resident on the current CUDA device."""
+
+    def __init__(self, handle: ctypes.c_void_p, nU: int, nV: int, m_in: int):
+        self._h = handle
+        self.nU, self.nV, self.m_in = nU, nV, m_in
+
+    # -- construction ---------------------------------------------------
+    @classmethod
+    def from_edges(cls, nU: int, nV: int, u, v, stream=None) -> "Graph":
+        lib = load_library()
+        torch = _torch()
+        pu, du, ku = _edge_arg(u, torch)
+        pv, dv, kv = _edge_arg(v, torch)
+        if du != dv:
+            raise ValueError("u and v must both be on the device or both on the host")
+        m = int(ku.shape[0])
+        if int(kv.shape[0]) != m:
+            raise ValueError("u and v differ in length")
+        h = ctypes.c_void_p()
+        _check(lib.pb_graph_from_edges(nU, nV, m, pu, pv, du, _stream(stream), ctypes.byref(h)))
+        return cls(h, nU, nV, m)
+
+    def free(self):
+        if self._h:
+            load_library().pb_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    # -- PREPROCESS -----------------------------------------------------
+    def rank(self, kind: str = "degree", stream=None) -> "Graph":
+        _check(load_library().pb_rank(self._h, RANKS[kind], _stream(stream)))
+        return self
+
+    def rank_custom(self, rank_of, stream=None) -> "Graph":
+        torch = _torch()
+        p, dev, keep = _edge_arg(rank_of, torch)
+        _check(load_library().pb_rank_custom(self._h, p, dev, _stream(stream)))
+        return self
+
+    def ranks(self, stream=None) -> np.ndarray:
+        out = np.empty(self.nU + self.nV, np.uint32)
+        _check(load_library().pb_graph_ranks(self._h, ctypes.c_void_p(out.ctypes.data), 0, _stream(stream)))
+        return out
+
+    @property
+    def wedges(self) -> int:
+        W = ctypes.c_uint64()
+        _check(load_library().pb_wedge_count(self._h, ctypes.byref(W)))
+        return int(W.value)
+
+    def info(self) -> GraphInfo:
+        inf = GraphInfo()
+        _check(load_library().pb_graph_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    # -- counting -------------------------------------------------------
+    def count_global(self, agg: str = "auto", scratch_bytes: int = 0, stream=None) -> int:
+        out = ctypes.c_uint64()
+        _check(load_library().pb_count_global(self._h, AGGS[agg], scratch_bytes, ctypes.byref(out),
+                                              _stream(stream)))
+        return int(out.value)
+
+    def count_vertex(self, agg: str = "auto", scratch_bytes: int = 0, on_device: bool = False, stream=None):
+        c = self.count_all(agg, scratch_bytes, glob=False, vertex=True, edge=False, on_device=on_device,
+                           stream=stream)
+        return c.per_vertex_U, c.per_vertex_V
+
+    def count_edge(self, agg: str = "auto", scratch_bytes: int = 0, on_device: bool = False, stream=None):
+        return self.count_all(agg, scratch_bytes, glob=False, vertex=False, edge=True, on_device=on_device,
+                              stream=stream).per_edge
+
+    def count_all(self, agg: str = "auto", scratch_bytes: int = 0, glob: bool = True, vertex: bool = True,
+                  edge: bool = True, on_device: bool = False, out=None, stream=None) -> Counts:
+        """One wedge pass producing any of the three outputs.  Host outputs are
+        uint64 numpy arrays; device outputs are int64 CUDA tensors holding the
+        uint64 bit patterns (``out`` may pass preallocated ones as a dict)."""
+        lib = load_library()
+        torch = _torch()
+        g = ctypes.c_uint64() if glob else None
+        U = V = E = None
+        if on_device:
+            out = out or {}
+            if vertex:
+                U = out.get("U", torch.empty(self.nU, dtype=torch.int64, device="cuda"))
+                V = out.get("V", torch.empty(self.nV, dtype=torch.int64, device="cuda"))
+            if edge:
+                E = out.get("E", torch.empty(self.m_in, dtype=torch.int64, device="cuda"))
+            ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        else:
+            out = out or {}
+            if vertex:
+                U = out.get("U", np.empty(self.nU, np.uint64))
+                V = out.get("V", np.empty(self.nV, np.uint64))
+            if edge:
+                E = out.get("E", np.empty(self.m_in, np.uint64))
+            ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+        _check(lib.pb_count_all(self._h, AGGS[agg], scratch_bytes, ctypes.byref(g) if g is not None else None,
+                                ptr(U), ptr(V), ptr(E), int(on_device), _stream(stream)))
+        return Counts(int(g.value) if g is not None else None, U, V, E)

@@ -1,0 +1,277 @@
+// The C ABI (include/pb.h): argument checks, device selection, memory
+// helpers, error reporting.  Every entry point returns a status; none aborts.
+#include <cstdarg>
+#include <mutex>
+#include <new>
+
+#include "pb_common.cuh"
+
+namespace pb {
+
+static thread_local std::string t_err;
+static std::atomic<uint64_t> g_launches{0};
+
+pb_status fail(pb_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+pb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  cudaGetLastError();  // clear a sticky launch error where possible
+  if (e == cudaErrorMemoryAllocation)
+    return fail(PB_ERR_NOMEM, "%s: out of device memory (%s:%d)", what, file, line);
+  return fail(PB_ERR_CUDA, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+void clear_error() { t_err.clear(); }
+void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Stream-ordered allocation from the device's default pool.  The pool keeps
+// freed memory (release threshold raised once per device) so repeated calls do
+// not return memory to the driver between calls.
+static std::mutex g_pool_mu;
+static bool g_pool_ready[64];
+
+pb_status dalloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_ready[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      cudaGetLastError();
+      g_pool_ready[dev] = true;
+    }
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
+  }
+  return PB_OK;
+}
+
+void dfree(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+pb_status ensure_scratch(pb_graph *g, size_t bytes, cudaStream_t s) {
+  if (g->scratch_cap >= bytes) return PB_OK;
+  PB_CUDA(cudaStreamSynchronize(s));
+  if (g->scratch) cudaFree(g->scratch);
+  g->scratch = nullptr;
+  g->scratch_cap = 0;
+  PB_CUDA(cudaMalloc(&g->scratch, bytes));
+  g->scratch_cap = bytes;
+  return PB_OK;
+}
+
+int sm_count(int device) {
+  static int cached[64] = {0};
+  if (device >= 0 && device < 64 && cached[device]) return cached[device];
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  if (v <= 0) v = 1;
+  if (device >= 0 && device < 64) cached[device] = v;
+  return v;
+}
+
+static void free_graph(pb_graph *g) {
+  if (!g) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  free_ranked(g);
+  cudaFree(g->in2c); cudaFree(g->eu); cudaFree(g->ev); cudaFree(g->deg);
+  cudaFree(g->scratch); cudaFree(g->pv); cudaFree(g->es); cudaFree(g->acc);
+  cudaGetLastError();
+  cudaSetDevice(cur);
+  delete g;
+}
+
+// Makes g's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" {
+
+const char *pb_last_error(void) { return t_err.c_str(); }
+
+const char *pb_status_string(pb_status s) {
+  switch (s) {
+    case PB_OK: return "PB_OK";
+    case PB_ERR_INVALID: return "PB_ERR_INVALID";
+    case PB_ERR_NOMEM: return "PB_ERR_NOMEM";
+    case PB_ERR_CUDA: return "PB_ERR_CUDA";
+    case PB_ERR_SCRATCH: return "PB_ERR_SCRATCH";
+    case PB_ERR_TIMEOUT: return "PB_ERR_TIMEOUT";
+    case PB_ERR_OVERFLOW: return "PB_ERR_OVERFLOW";
+  }
+  return "PB_ERR_UNKNOWN";
+}
+
+uint64_t pb_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v,
+                              int on_device, void *stream, pb_graph **out) {
+  clear_error();
+  if (!out) return fail(PB_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (m > 0 && (!u || !v)) return fail(PB_ERR_INVALID, "u or v is NULL");
+  uint64_t n = static_cast<uint64_t>(nU) + nV;
+  if (n == 0) return fail(PB_ERR_INVALID, "graph has no vertices");
+  if (n >= (uint64_t(1) << 31)) return fail(PB_ERR_INVALID, "nU + nV must be below 2^31");
+  if (m >= (uint64_t(1) << 32) - 1) return fail(PB_ERR_INVALID, "too many input edges (m >= 2^32-1)");
+  pb_graph *g = new (std::nothrow) pb_graph();
+  if (!g) return fail(PB_ERR_NOMEM, "host allocation failed");
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    delete g;
+    return fail(PB_ERR_CUDA, "no CUDA device");
+  }
+  g->nU = nU;
+  g->nV = nV;
+  g->n = n;
+  g->m_in = m;
+  g->bitsN = bits_for(n - 1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pb_status st = build_graph(g, u, v, on_device, s);
+  if (st == PB_OK) st = rank_graph(g, PB_RANK_SIDE, nullptr, 0, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st == PB_OK && e != cudaSuccess) st = cuda_fail(e, "graph build", __FILE__, __LINE__);
+  if (st != PB_OK) {
+    std::string keep = t_err;
+    free_graph(g);
+    t_err = keep;
+    return st;
+  }
+  *out = g;
+  return PB_OK;
+}
+
+pb_status pb_rank(pb_graph *g, pb_rank_kind kind, void *stream) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  if (kind < PB_RANK_SIDE || kind > PB_RANK_APPROX_DEGREE) return fail(PB_ERR_INVALID, "unknown rank kind %d", (int)kind);
+  DeviceGuard dg(g->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PB_TRY(rank_graph(g, kind, nullptr, 0, s));
+  PB_CUDA(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
+pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, void *stream) {
+  clear_error();
+  if (!g || !rank_of) return fail(PB_ERR_INVALID, "graph or rank_of is NULL");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PB_TRY(rank_graph(g, 3, rank_of, on_device, s));
+  PB_CUDA(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
+pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream) {
+  clear_error();
+  if (!g || !rank_of) return fail(PB_ERR_INVALID, "graph or rank_of is NULL");
+  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PB_CUDA(cudaMemcpyAsync(rank_of, g->rank, g->n * sizeof(uint32_t),
+                          out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  PB_CUDA(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
+pb_status pb_count_all(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out_global, uint64_t *out_U,
+                       uint64_t *out_V, uint64_t *out_E, int out_on_device, void *stream) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  DeviceGuard dg(g->device);
+  CountOut o;
+  o.global = out_global;
+  o.U = out_U;
+  o.V = out_V;
+  o.E = out_E;
+  o.on_device = out_on_device;
+  return count_all(g, static_cast<int>(agg), scratch_bytes, o, static_cast<cudaStream_t>(stream));
+}
+
+pb_status pb_count_global(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out, void *stream) {
+  if (!out) return fail(PB_ERR_INVALID, "out is NULL");
+  return pb_count_all(g, agg, scratch_bytes, out, nullptr, nullptr, nullptr, 0, stream);
+}
+
+pb_status pb_count_vertex(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out_U, uint64_t *out_V,
+                          int out_on_device, void *stream) {
+  if (!out_U && !out_V) return fail(PB_ERR_INVALID, "both outputs are NULL");
+  return pb_count_all(g, agg, scratch_bytes, nullptr, out_U, out_V, nullptr, out_on_device, stream);
+}
+
+pb_status pb_count_edge(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out_E, int out_on_device,
+                        void *stream) {
+  if (!out_E) return fail(PB_ERR_INVALID, "out_E is NULL");
+  return pb_count_all(g, agg, scratch_bytes, nullptr, nullptr, nullptr, out_E, out_on_device, stream);
+}
+
+pb_status pb_wedge_count(const pb_graph *g, uint64_t *W) {
+  clear_error();
+  if (!g || !W) return fail(PB_ERR_INVALID, "graph or W is NULL");
+  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
+  *W = g->W;
+  return PB_OK;
+}
+
+pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info) {
+  clear_error();
+  if (!g || !info) return fail(PB_ERR_INVALID, "graph or info is NULL");
+  info->nU = g->nU;
+  info->nV = g->nV;
+  info->m_in = g->m_in;
+  info->m = g->m;
+  info->max_deg_U = g->maxdegU;
+  info->max_deg_V = g->maxdegV;
+  info->rank_kind = g->rank_kind;
+  info->W = g->W;
+  info->max_wedges_x1 = g->maxw;
+  uint64_t b = 0;
+  b += (g->m_in + 1) * 4 + 2 * (g->m + 1) * 4 + (g->n + 1) * 4;            // input map, edges, degrees
+  if (g->rank_kind >= 0) b += 4 * (g->n + 1) * 4 + (g->n + 1) * 8 + 2 * (2 * g->m + 1) * 4 + 2 * (g->m + 1) * 4;
+  if (g->pv) b += (g->n + 1) * 8;
+  if (g->es) b += (2 * g->m + 1) * 8;
+  b += g->scratch_cap;
+  info->device_bytes = b;
+  return PB_OK;
+}
+
+pb_status pb_graph_free(pb_graph *g) {
+  clear_error();
+  free_graph(g);
+  return PB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1038 @@
+// Wedge retrieval (Algorithm 2) fused with wedge aggregation (GET-FREQ,
+// Sec. "Wedge aggregation") and butterfly aggregation with atomic adds
+// (Sec. "Butterfly aggregation"; Algorithms 3 and 4).
+//
+// For a first endpoint x1 the wedges are ((x1, x2), y) with y in the first
+// deg_x1(x1) slots of x1's list and x2 in the first deg_x1(y) slots of y's
+// list (lists are sorted by decreasing rank).  The wedges of x1 are grouped by
+// x2; the group size d(x1, x2) = |N(x1) n N(x2)| restricted to centres ranked
+// above x1.  Then, per group:
+//   global += C(d, 2); pv[x1] += C(d, 2); pv[x2] += C(d, 2)          (Eq. 1)
+// and per wedge (second pass over the same wedges, d still in scratch):
+//   pv[y] += d - 1; e(x1, y) += d - 1; e(x2, y) += d - 1             (Eq. 2)
+// Edge contributions land on adjacency slots: e(x2, y) on the slot of x2 in
+// y's list, e(x1, y) on the slot of y in x1's list; an edge's count is the sum
+// of its two slots.
+//
+// Work split: first endpoints are binned by their wedge count (prefix sums of
+// the PREPROCESS step):
+//   light  (<= 512 wedges)   one warp per x1, hash table in shared memory;
+//   medium (<= 4096 wedges)  one block per x1, hash table in shared memory;
+//   heavy                    one thread-block cluster per x1, aggregation in
+//                            device memory: a dense histogram over all second
+//                            endpoints with a touched list, or an
+//                            open-addressing hash table.
+// Inside a warp / block / cluster the wedges of a chunk of neighbours are
+// flattened with a prefix sum over deg_x1(y) and spread evenly over threads.
+#include <cooperative_groups.h>
+
+#include "pb_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pb {
+
+struct CArgs {
+  const uint32_t *__restrict__ off;
+  const uint32_t *__restrict__ adj;
+  const uint32_t *__restrict__ cpos;
+  const uint32_t *__restrict__ degp;
+  const uint64_t *__restrict__ wpre;
+  uint64_t n;
+  unsigned long long *pv;   // [n] rank space, or null
+  unsigned long long *es;   // [2m] per slot, or null
+  unsigned long long *acc;  // [0] global, [1] overflow, [2..] work queues
+};
+
+enum { ACC_GLOBAL = 0, ACC_OVF = 1, ACC_QMED = 2, ACC_QHEAVY = 3, ACC_NLIGHT = 4, ACC_NMED = 5,
+       ACC_NHEAVY = 6, ACC_ERR = 7, ACC_WORDS = 8 };
+
+// Probe loops are bounded by the table size; running past it (impossible at
+// load <= 1/2 unless scratch is corrupt) records an error instead of spinning.
+
+constexpr uint32_t LIGHT_MAX = 512;   // wedges of a light first endpoint
+constexpr int LW_THREADS = 256;
+constexpr int LW_WARPS = LW_THREADS / 32;
+constexpr int LW_CAP = 1024;          // per-warp table entries (>= 2 * LIGHT_MAX)
+constexpr uint32_t MED_MAX = 4096;
+constexpr int MB_THREADS = 512;
+constexpr int MB_CAP = 8192;          // per-block table entries (>= 2 * MED_MAX)
+constexpr int HB_THREADS = 1024;
+
+__device__ __forceinline__ void add_global(unsigned long long *acc, unsigned long long v) {
+  if (!v) return;
+  unsigned long long old = atomicAdd(&acc[ACC_GLOBAL], v);
+  if (old + v < old) atomicAdd(&acc[ACC_OVF], 1ull);
+}
+
+__device__ __forceinline__ uint32_t hash_home(uint32_t x, int lg) {
+  return (x * 0x9E3779B1u) >> (32 - lg);
+}
+
+// Shared-memory open addressing (linear probing, atomic-add combine).
+__device__ __forceinline__ void sh_add(uint32_t *key, uint32_t *cnt, int lg, uint32_t x,
+                                       unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t h = hash_home(x, lg);
+  for (uint32_t probe = 0;; probe++) {
+    if (probe > mask) { atomicOr(err, 1ull); return; }
+    uint32_t k = reinterpret_cast<volatile uint32_t *>(key)[h];
+    if (k == x) break;
+    if (k == EMPTY) {
+      uint32_t prev = atomicCAS(&key[h], EMPTY, x);
+      if (prev == EMPTY || prev == x) break;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicAdd(&cnt[h], 1u);
+}
+
+__device__ __forceinline__ uint32_t sh_get(const uint32_t *key, const uint32_t *cnt, int lg, uint32_t x,
+                                           unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t h = hash_home(x, lg);
+  for (uint32_t probe = 0; key[h] != x; probe++) {
+    if (probe > mask) { atomicOr(err, 2ull); return 0; }
+    h = (h + 1) & mask;
+  }
+  return cnt[h];
+}
+
+__device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t x1) {
+  uint64_t dmax = wc < n - 1 - x1 ? wc : n - 1 - x1;  // distinct second endpoints
+  int lg = 5;
+  while ((uint64_t(1) << lg) < 2 * dmax) lg++;
+  return lg;
+}
+
+// Warp-level: which lane's neighbour owns flattened wedge index wi, and the
+// adjacency slot of that wedge's second endpoint.
+__device__ __forceinline__ void warp_locate(uint32_t incl, uint32_t c, uint32_t oy, uint32_t wi,
+                                            uint32_t &src, uint32_t &slot) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1) {
+    uint32_t v = __shfl_sync(FULL, incl, lo + step - 1);
+    if (v <= wi) lo += step;
+  }
+  uint32_t s_incl = __shfl_sync(FULL, incl, lo);
+  uint32_t s_c = __shfl_sync(FULL, c, lo);
+  uint32_t s_oy = __shfl_sync(FULL, oy, lo);
+  src = static_cast<uint32_t>(lo);
+  slot = s_oy + (wi - (s_incl - s_c));
+}
+
+// ---------------------------------------------------------------------------
+// Light tier: one warp per first endpoint.
+template <bool PV, bool PE>
+__global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *__restrict__ list,
+                                                      uint32_t nlist) {
+  extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP counts
+  __shared__ unsigned long long s_sum[LW_WARPS][32];
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t *key = dsm + w * 2 * LW_CAP, *cnt = key + LW_CAP;
+  unsigned long long gacc = 0;
+  if (PV || PE) s_sum[w][lane] = 0;
+  for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
+    const uint32_t x1 = list[it];
+    const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
+    const int lg = table_lg(wc, a.n, x1);
+    const uint32_t cap = 1u << lg;
+    for (uint32_t t = lane; t < cap; t += 32) { key[t] = EMPTY; cnt[t] = 0; }
+    __syncwarp();
+    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
+      const uint32_t i = k0 + lane;
+      const bool v = i < dp;
+      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0, oy = v ? a.off[y] : 0;
+      const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
+      for (uint32_t wb = 0; wb < tot; wb += 32) {
+        const uint32_t wi = wb + lane;
+        uint32_t src, slot;
+        warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
+        if (wi < tot) sh_add(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
+      }
+    }
+    __syncwarp();
+    unsigned long long own = 0;
+    for (uint32_t t = lane; t < cap; t += 32) {
+      uint32_t k = key[t];
+      if (k != EMPTY) {
+        unsigned long long d = cnt[t], b = d * (d - 1) / 2;
+        own += b;
+        if (PV && b) atomicAdd(&a.pv[k], b);
+      }
+    }
+    own = warp_sum(own);
+    if (lane == 0) {
+      gacc += own;
+      if (PV && own) atomicAdd(&a.pv[x1], own);
+    }
+    if (PV || PE) {
+      for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
+        const uint32_t i = k0 + lane;
+        const bool v = i < dp;
+        const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0, oy = v ? a.off[y] : 0;
+        const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
+        for (uint32_t wb = 0; wb < tot; wb += 32) {
+          const uint32_t wi = wb + lane;
+          uint32_t src, slot;
+          warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
+          if (wi < tot) {
+            uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
+            if (d > 1) {
+              unsigned long long t = d - 1;
+              if (PE) atomicAdd(&a.es[slot], t);
+              atomicAdd(&s_sum[w][src], t);
+            }
+          }
+        }
+        __syncwarp();
+        if (v) {
+          unsigned long long sm = s_sum[w][lane];
+          if (sm) {
+            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PE) atomicAdd(&a.es[base + i], sm);
+            s_sum[w][lane] = 0;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) add_global(a.acc, gacc);
+}
+
+// ---------------------------------------------------------------------------
+// Block-level flattening of a chunk of neighbours.
+__device__ __forceinline__ uint32_t block_find(const uint32_t *s_incl, uint32_t nb, uint32_t wi) {
+  uint32_t lo = 0, hi = nb - 1;  // first index with s_incl > wi
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (s_incl[mid] > wi) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Medium tier: one block per first endpoint, table in (dynamic) shared memory.
+template <bool PV, bool PE>
+__global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *__restrict__ list,
+                                                       uint32_t nlist) {
+  extern __shared__ uint32_t dsm[];
+  uint32_t *key = dsm, *cnt = dsm + MB_CAP;
+  __shared__ uint32_t s_incl[MB_THREADS], s_ex[MB_THREADS], s_oy[MB_THREADS];
+  __shared__ unsigned long long s_sum[MB_THREADS];
+  __shared__ uint32_t s_w[33];
+  __shared__ unsigned long long s_w64[33];
+  __shared__ uint32_t s_item;
+  const uint32_t tid = threadIdx.x;
+  unsigned long long gacc = 0;
+  if (PV || PE) s_sum[tid] = 0;
+  for (;;) {
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QMED], 1ull));
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= nlist) break;
+    const uint32_t x1 = list[it];
+    const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
+    const int lg = table_lg(wc, a.n, x1);
+    const uint32_t cap = 1u << lg;
+    for (uint32_t t = tid; t < cap; t += MB_THREADS) { key[t] = EMPTY; cnt[t] = 0; }
+    __syncthreads();
+    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
+      const uint32_t i = k0 + tid;
+      const bool v = i < dp;
+      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+      uint32_t tot;
+      const uint32_t incl = block_incl_scan(c, s_w, &tot);
+      s_incl[tid] = incl;
+      s_ex[tid] = incl - c;
+      s_oy[tid] = v ? a.off[y] : 0;
+      __syncthreads();
+      for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
+        uint32_t src = block_find(s_incl, MB_THREADS, wi);
+        sh_add(key, cnt, lg, a.adj[s_oy[src] + (wi - s_ex[src])], &a.acc[ACC_ERR]);
+      }
+      __syncthreads();
+    }
+    unsigned long long own = 0;
+    for (uint32_t t = tid; t < cap; t += MB_THREADS) {
+      uint32_t k = key[t];
+      if (k != EMPTY) {
+        unsigned long long d = cnt[t], b = d * (d - 1) / 2;
+        own += b;
+        if (PV && b) atomicAdd(&a.pv[k], b);
+      }
+    }
+    own = block_sum(own, s_w64);
+    if (tid == 0) {
+      gacc += own;
+      if (PV && own) atomicAdd(&a.pv[x1], own);
+    }
+    if (PV || PE) {
+      for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
+        const uint32_t i = k0 + tid;
+        const bool v = i < dp;
+        const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(c, s_w, &tot);
+        s_incl[tid] = incl;
+        s_ex[tid] = incl - c;
+        s_oy[tid] = v ? a.off[y] : 0;
+        __syncthreads();
+        for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
+          uint32_t src = block_find(s_incl, MB_THREADS, wi);
+          uint32_t slot = s_oy[src] + (wi - s_ex[src]);
+          uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
+          if (d > 1) {
+            unsigned long long t = d - 1;
+            if (PE) atomicAdd(&a.es[slot], t);
+            atomicAdd(&s_sum[src], t);
+          }
+        }
+        __syncthreads();
+        if (v) {
+          unsigned long long sm = s_sum[tid];
+          if (sm) {
+            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PE) atomicAdd(&a.es[base + i], sm);
+            s_sum[tid] = 0;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) add_global(a.acc, gacc);
+}
+
+// ---------------------------------------------------------------------------
+// Heavy tier: one cluster per first endpoint; each cluster owns one slot of
+// device-memory scratch.  The blocks of the cluster walk the same neighbour
+// chunks and take equal shares of every chunk's wedges.  Phases are separated
+// by cluster barriers (release/acquire at cluster scope); scratch written by
+// other blocks is read through L2 (ld.global.cg).
+struct HeavySlots {
+  uint32_t *A;        // dense: [nslots][n] counts (all zero between uses)
+  uint32_t *T;        // dense: [nslots][tcap] touched second endpoints
+  uint32_t *hkey;     // hash:  [nslots][hcap] keys (EMPTY between uses)
+  uint32_t *hval;     // hash:  [nslots][hcap] counts
+  uint32_t *tcnt;     // [nslots][2] touched counters (alternating)
+  uint32_t *item;     // [nslots] current work item of the slot
+  uint64_t n, tcap, hcap;
+};
+
+template <bool DENSE>
+__device__ __forceinline__ void heavy_insert(const HeavySlots &h, uint32_t slot, uint32_t *A, uint32_t *T,
+                                             uint32_t *tc, int lg, uint32_t x2, bool act,
+                                             unsigned long long *err) {
+  if (DENSE) {
+    bool isnew = false;
+    if (act) isnew = atomicAdd(&A[x2], 1u) == 0u;
+    uint32_t bm = __ballot_sync(FULL, isnew);
+    if (bm) {
+      uint32_t leader = __ffs(bm) - 1, b0 = 0;
+      if (lane_id() == leader) b0 = atomicAdd(tc, static_cast<uint32_t>(__popc(bm)));
+      b0 = __shfl_sync(FULL, b0, leader);
+      if (isnew) {
+        uint32_t pos = b0 + __popc(bm & lanemask_lt());
+        if (pos < h.tcap) T[pos] = x2;
+        else atomicOr(err, 16ull);
+      }
+    }
+  } else if (act) {
+    uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
+    uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
+    const uint32_t mask = (1u << lg) - 1;
+    uint32_t p = hash_home(x2, lg);
+    for (uint32_t probe = 0;; probe++) {
+      if (probe > mask) { atomicOr(err, 4ull); return; }
+      uint32_t k = __ldcg(&key[p]);
+      if (k == EMPTY) k = atomicCAS(&key[p], EMPTY, x2);
+      if (k == EMPTY || k == x2) break;
+      p = (p + 1) & mask;
+    }
+    atomicAdd(&val[p], 1u);
+  }
+}
+
+template <bool DENSE>
+__device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot, const uint32_t *A, int lg,
+                                              uint32_t x2, unsigned long long *err) {
+  if (DENSE) return __ldcg(&A[x2]);
+  const uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
+  const uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t p = hash_home(x2, lg);
+  for (uint32_t probe = 0; __ldcg(&key[p]) != x2; probe++) {
+    if (probe > mask) { atomicOr(err, 8ull); return 0; }
+    p = (p + 1) & mask;
+  }
+  return __ldcg(&val[p]);
+}
+
+template <bool PV, bool PE, bool DENSE>
+__global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *__restrict__ list,
+                                                      uint32_t nlist, HeavySlots h) {
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
+  const uint32_t slot = blockIdx.x / csize;
+  const uint32_t tid = threadIdx.x;
+  __shared__ uint32_t s_incl[HB_THREADS], s_ex[HB_THREADS], s_oy[HB_THREADS];
+  __shared__ unsigned long long s_sum[HB_THREADS];
+  __shared__ uint32_t s_w[33];
+  __shared__ unsigned long long s_w64[33];
+  uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.n : nullptr;
+  uint32_t *T = DENSE ? h.T + static_cast<size_t>(slot) * h.tcap : nullptr;
+  unsigned long long gacc = 0;
+  if (PV || PE) s_sum[tid] = 0;
+  for (uint32_t k = 0;; k++) {
+    if (crank == 0 && tid == 0) h.item[slot] = static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QHEAVY], 1ull));
+    cl.sync();
+    const uint32_t it = __ldcg(&h.item[slot]);
+    if (it >= nlist) break;
+    uint32_t *tc = &h.tcnt[2 * slot + (k & 1)];
+    if (crank == 0 && tid == 0) h.tcnt[2 * slot + ((k + 1) & 1)] = 0;
+    const uint32_t x1 = list[it];
+    const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
+    const int lg = DENSE ? 0 : table_lg(wc, a.n, x1);
+    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    // ---- aggregate
+    for (uint32_t k0 = 0; k0 < dp; k0 += HB_THREADS) {
+      const uint32_t i = k0 + tid;
+      const bool v = i < dp;
+      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+      uint32_t tot;
+      const uint32_t incl = block_incl_scan(c, s_w, &tot);
+      s_incl[tid] = incl;
+      s_ex[tid] = incl - c;
+      s_oy[tid] = v ? a.off[y] : 0;
+      __syncthreads();
+      const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(tot) * crank / csize);
+      const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(tot) * (crank + 1) / csize);
+      for (uint32_t wb = lo; wb < hi; wb += HB_THREADS) {
+        const uint32_t wi = wb + tid;
+        const bool act = wi < hi;
+        uint32_t x2 = 0;
+        if (act) {
+          uint32_t src = block_find(s_incl, HB_THREADS, wi);
+          x2 = a.adj[s_oy[src] + (wi - s_ex[src])];
+        }
+        heavy_insert<DENSE>(h, slot, A, T, tc, lg, x2, act, &a.acc[ACC_ERR]);
+      }
+      __syncthreads();
+    }
+    cl.sync();
+    // ---- endpoints: C(d, 2) per distinct second endpoint
+    unsigned long long own = 0;
+    if (DENSE) {
+      const uint32_t nt = __ldcg(tc);
+      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) {
+        uint32_t x2 = __ldcg(&T[t]);
+        unsigned long long d = __ldcg(&A[x2]), b = d * (d - 1) / 2;
+        own += b;
+        if (PV && b) atomicAdd(&a.pv[x2], b);
+      }
+    } else {
+      const uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
+      const uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
+      const uint32_t cap = 1u << lg;
+      for (uint32_t t = crank * HB_THREADS + tid; t < cap; t += csize * HB_THREADS) {
+        uint32_t kk = __ldcg(&key[t]);
+        if (kk != EMPTY) {
+          unsigned long long d = __ldcg(&val[t]), b = d * (d - 1) / 2;
+          own += b;
+          if (PV && b) atomicAdd(&a.pv[kk], b);
+        }
+      }
+    }
+    own = block_sum(own, s_w64);
+    if (tid == 0) {
+      gacc += own;
+      if (PV && own) atomicAdd(&a.pv[x1], own);
+    }
+    // ---- centres and edges
+    if (PV || PE) {
+      for (uint32_t k0 = 0; k0 < dp; k0 += HB_THREADS) {
+        const uint32_t i = k0 + tid;
+        const bool v = i < dp;
+        const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(c, s_w, &tot);
+        s_incl[tid] = incl;
+        s_ex[tid] = incl - c;
+        s_oy[tid] = v ? a.off[y] : 0;
+        __syncthreads();
+        const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(tot) * crank / csize);
+        const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(tot) * (crank + 1) / csize);
+        for (uint32_t wi = lo + tid; wi < hi; wi += HB_THREADS) {
+          uint32_t src = block_find(s_incl, HB_THREADS, wi);
+          uint32_t sl = s_oy[src] + (wi - s_ex[src]);
+          uint32_t d = heavy_get<DENSE>(h, slot, A, lg, a.adj[sl], &a.acc[ACC_ERR]);
+          if (d > 1) {
+            unsigned long long t = d - 1;
+            if (PE) atomicAdd(&a.es[sl], t);
+            atomicAdd(&s_sum[src], t);
+          }
+        }
+        __syncthreads();
+        if (v) {
+          unsigned long long sm = s_sum[tid];
+          if (sm) {
+            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PE) atomicAdd(&a.es[base + i], sm);
+            s_sum[tid] = 0;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    cl.sync();
+    // ---- restore the slot to all-zero / all-empty
+    if (DENSE) {
+      const uint32_t nt = __ldcg(tc);
+      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) A[__ldcg(&T[t])] = 0;
+    } else {
+      uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
+      uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
+      const uint32_t cap = 1u << lg;
+      for (uint32_t t = crank * HB_THREADS + tid; t < cap; t += csize * HB_THREADS) {
+        key[t] = EMPTY;
+        val[t] = 0;
+      }
+    }
+  }
+  if (tid == 0) add_global(a.acc, gacc);
+}
+
+// ---------------------------------------------------------------------------
+// Sort aggregation: the wedges of a chunk of first endpoints [lo, hi) are
+// materialised as keys ((x1 - lo) << bitsN) | x2, radix-sorted, and grouped;
+// a group's length is d(x1, x2).  The chunk is sized so that its wedges fit
+// the scratch budget (the paper's limit on wedges processed at once).  The
+// second pass re-walks the chunk's wedges and finds d by binary search in the
+// sorted group keys of its first endpoint.
+
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *a, uint32_t lo, uint32_t hi, uint64_t k) {
+  while (lo < hi) {
+    uint32_t mid = lo + ((hi - lo) >> 1);
+    if (a[mid] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <bool PV, bool PE, bool EMIT>
+__global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, uint32_t hi, uint64_t wbase,
+                                                          int bitsN, uint64_t *__restrict__ keys,
+                                                          const uint64_t *__restrict__ ukey,
+                                                          const uint32_t *__restrict__ ud,
+                                                          const uint32_t *__restrict__ seg) {
+  __shared__ uint32_t s_incl[MB_THREADS], s_ex[MB_THREADS], s_oy[MB_THREADS];
+  __shared__ unsigned long long s_sum[MB_THREADS];
+  __shared__ uint32_t s_w[33];
+  __shared__ uint32_t s_item;
+  const uint32_t tid = threadIdx.x;
+  if (!EMIT) s_sum[tid] = 0;
+  for (;;) {
+    if (tid == 0) s_item = lo + static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QMED], 1ull));
+    __syncthreads();
+    const uint32_t x1 = s_item;
+    if (x1 >= hi) break;
+    const uint64_t kx = static_cast<uint64_t>(x1 - lo) << bitsN;
+    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    uint64_t *out = EMIT ? keys + (a.wpre[x1] - wbase) : nullptr;
+    uint32_t s0 = 0, s1 = 0;
+    if (!EMIT) { s0 = seg[x1 - lo]; s1 = seg[x1 - lo + 1]; }
+    uint64_t done = 0;
+    for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
+      const uint32_t i = k0 + tid;
+      const bool v = i < dp;
+      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+      uint32_t tot;
+      const uint32_t incl = block_incl_scan(c, s_w, &tot);
+      s_incl[tid] = incl;
+      s_ex[tid] = incl - c;
+      s_oy[tid] = v ? a.off[y] : 0;
+      __syncthreads();
+      for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
+        uint32_t src = block_find(s_incl, MB_THREADS, wi);
+        uint32_t slot = s_oy[src] + (wi - s_ex[src]);
+        uint32_t x2 = a.adj[slot];
+        if (EMIT) {
+          out[done + wi] = kx | x2;
+        } else {
+          uint32_t r = lower_bound_u64(ukey, s0, s1, kx | x2);
+          uint32_t d = (r < s1 && ukey[r] == (kx | x2)) ? ud[r] : 0;
+          if (d == 0) atomicOr(&a.acc[ACC_ERR], 32ull);
+          if (d > 1) {
+            unsigned long long t = d - 1;
+            if (PE) atomicAdd(&a.es[slot], t);
+            atomicAdd(&s_sum[src], t);
+          }
+        }
+      }
+      __syncthreads();
+      if (!EMIT && v) {
+        unsigned long long sm = s_sum[tid];
+        if (sm) {
+          if (PV) atomicAdd(&a.pv[y], sm);
+          if (PE) atomicAdd(&a.es[base + i], sm);
+          s_sum[tid] = 0;
+        }
+      }
+      done += tot;
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_runs(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ head,
+                       const uint32_t *__restrict__ cid, uint64_t cnt, uint64_t *__restrict__ ukey,
+                       uint32_t *__restrict__ rstart) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    if (head[i]) {
+      uint32_t r = cid[i];
+      ukey[r] = keys[i];
+      rstart[r] = static_cast<uint32_t>(i);
+    }
+  }
+}
+
+template <bool PV>
+__global__ void k_run_sums(CArgs a, const uint64_t *__restrict__ ukey, const uint32_t *__restrict__ rstart,
+                           uint32_t nr, uint32_t cnt, uint32_t lo, int bitsN, uint32_t *__restrict__ ud) {
+  __shared__ unsigned long long s_w64[33];
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
+  unsigned long long acc = 0;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+    uint32_t d = (r + 1 < nr ? rstart[r + 1] : cnt) - rstart[r];
+    ud[r] = d;
+    unsigned long long b = static_cast<unsigned long long>(d) * (d - 1) / 2;
+    acc += b;
+    if (PV && b) {
+      atomicAdd(&a.pv[lo + static_cast<uint32_t>(ukey[r] >> bitsN)], b);
+      atomicAdd(&a.pv[static_cast<uint32_t>(ukey[r] & mask)], b);
+    }
+  }
+  unsigned long long tot = block_sum(acc, s_w64);
+  if (threadIdx.x == 0) add_global(a.acc, tot);
+}
+
+__global__ void k_segments(const uint64_t *__restrict__ ukey, uint32_t nr, uint32_t nseg, int bitsN,
+                           uint32_t *__restrict__ seg) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= nseg; j += gridDim.x * blockDim.x)
+    seg[j] = lower_bound_u64(ukey, 0, nr, static_cast<uint64_t>(j) << bitsN);
+}
+
+// Largest hi in (lo, n] with wpre[hi] - wpre[lo] <= cap (at least lo + 1).
+__global__ void k_chunk_end(const uint64_t *__restrict__ wpre, uint64_t n, uint32_t lo, uint64_t cap,
+                            unsigned long long *out) {
+  uint64_t base = wpre[lo];
+  uint64_t l = lo + 1, h = n;  // answer in [lo+1, n]
+  while (l < h) {
+    uint64_t mid = (l + h + 1) >> 1;
+    if (wpre[mid] - base <= cap) l = mid;
+    else h = mid - 1;
+  }
+  out[0] = l;
+  out[1] = wpre[l] - base;
+}
+
+// ---------------------------------------------------------------------------
+// Tier classification.
+__global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64_t light_max, uint64_t med_max,
+                           uint32_t *__restrict__ light, uint32_t *__restrict__ med,
+                           uint64_t *__restrict__ heavy_keys, int bitsN, unsigned long long *acc) {
+  size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  size_t iters = (n + stride - 1) / stride;
+  for (size_t itn = 0; itn < iters; itn++) {
+    size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x + itn * stride;
+    uint64_t wc = x < n ? wpre[x + 1] - wpre[x] : 0;
+    int tier = wc == 0 ? 0 : (wc <= light_max ? 1 : (wc <= med_max ? 2 : 3));
+#pragma unroll
+    for (int t = 1; t <= 3; t++) {
+      uint32_t bm = __ballot_sync(FULL, tier == t);
+      if (!bm) continue;
+      uint32_t leader = __ffs(bm) - 1;
+      unsigned long long b0 = 0;
+      if (lane_id() == leader) b0 = atomicAdd(&acc[ACC_NLIGHT + t - 1], (unsigned long long)__popc(bm));
+      b0 = __shfl_sync(FULL, b0, leader);
+      if (tier == t) {
+        uint64_t at = b0 + __popc(bm & lanemask_lt());
+        if (t == 1) light[at] = static_cast<uint32_t>(x);
+        else if (t == 2) med[at] = static_cast<uint32_t>(x);
+        else {
+          // decreasing wedge count first (largest-first scheduling)
+          const uint64_t cmax = (uint64_t(1) << (63 - bitsN)) - 1;
+          uint64_t cw = wc < cmax ? wc : cmax;
+          heavy_keys[at] = ((cmax - cw) << bitsN) | x;
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_keys_low(const uint64_t *__restrict__ keys, uint32_t nk, int bitsN, uint32_t *__restrict__ out) {
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x)
+    out[i] = static_cast<uint32_t>(keys[i] & mask);
+}
+
+__global__ void k_max_wedges_list(const uint32_t *__restrict__ list, uint32_t nl, const uint64_t *__restrict__ wpre,
+                                  uint64_t n, unsigned long long *out) {
+  unsigned long long mx = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+    uint32_t x = list[i];
+    unsigned long long wc = wpre[x + 1] - wpre[x];
+    unsigned long long dm = wc < n - 1 - x ? wc : n - 1 - x;
+    mx = dm > mx ? dm : mx;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(FULL, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if (lane_id() == 0 && mx) atomicMax(out, mx);
+}
+
+// ---------------------------------------------------------------------------
+// Outputs back in id space / input order.
+__global__ void k_out_vertex(const unsigned long long *__restrict__ pv, const uint32_t *__restrict__ rank,
+                             uint32_t nU, uint32_t nV, uint64_t *__restrict__ outU, uint64_t *__restrict__ outV) {
+  const uint64_t n = static_cast<uint64_t>(nU) + nV;
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint64_t c = pv[rank[x]];
+    if (x < nU) {
+      if (outU) outU[x] = c;
+    } else if (outV) {
+      outV[x - nU] = c;
+    }
+  }
+}
+
+__global__ void k_out_edge(const unsigned long long *__restrict__ es, const uint32_t *__restrict__ slotA,
+                           const uint32_t *__restrict__ slotB, const uint32_t *__restrict__ in2c, uint64_t m_in,
+                           uint64_t *__restrict__ outE) {
+  for (size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < m_in;
+       k += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t e = in2c[k];
+    outE[k] = es[slotA[e]] + es[slotB[e]];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration.
+
+template <class K, class... Args>
+static pb_status launch_cluster(K kernel, unsigned grid, unsigned block, unsigned cl, cudaStream_t s,
+                                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  PB_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+  count_launch();
+  return PB_OK;
+}
+
+template <class K>
+static int max_clusters(K kernel, unsigned block, unsigned cl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl * 256);
+  cfg.blockDim = dim3(block);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc;
+}
+
+struct Plan {
+  int agg;
+  bool pv, pe;
+  uint64_t light_max, med_max;
+  bool dense;       // heavy tier uses dense histograms
+  unsigned cluster; // blocks per heavy first endpoint
+};
+
+template <bool PV, bool PE>
+static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t budget, cudaStream_t s) {
+  const uint64_t n = g->n;
+  unsigned long long hcnt[ACC_WORDS] = {0};
+  uint32_t *light = nullptr, *med = nullptr, *heavy = nullptr;
+  uint64_t *hkeys = nullptr;
+  unsigned long long *dmx = nullptr;
+  pb_status st = PB_OK;
+  const int sms = sm_count(g->device);
+  do {
+    if ((st = dalloc_t(&light, n + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&med, n + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&hkeys, n + 1, s)) != PB_OK) break;
+    k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->wpre, n, p.light_max, p.med_max, light, med, hkeys,
+                                                      g->bitsN, a.acc);
+    count_launch();
+    if (cudaMemcpyAsync(hcnt, a.acc, sizeof(hcnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "tier readback: %s", cudaGetErrorString(cudaGetLastError())); break; }
+    const uint32_t nl = static_cast<uint32_t>(hcnt[ACC_NLIGHT]), nm = static_cast<uint32_t>(hcnt[ACC_NMED]),
+                   nh = static_cast<uint32_t>(hcnt[ACC_NHEAVY]);
+    if (nl) {
+      const size_t smem = 2 * LW_WARPS * LW_CAP * sizeof(uint32_t);
+      PB_CUDA(cudaFuncSetAttribute(k_light<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_light<PV, PE>, LW_THREADS, smem);
+      unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
+      unsigned need = (nl + LW_WARPS - 1) / LW_WARPS;
+      PB_LAUNCH((k_light<PV, PE>), grid < need ? grid : need, LW_THREADS, smem, s, a, light, nl);
+    }
+    if (nm) {
+      const size_t smem = 2 * MB_CAP * sizeof(uint32_t);
+      PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE>, MB_THREADS, smem);
+      unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
+      PB_LAUNCH((k_medium<PV, PE>), grid < nm ? grid : nm, MB_THREADS, smem, s, a, med, nm);
+    }
+    if (nh) {
+      if ((st = radix_sort(hkeys, nullptr, nh, 64 - 1, s)) != PB_OK) break;
+      if ((st = dalloc_t(&heavy, nh, s)) != PB_OK) break;
+      k_keys_low<<<grid_for(nh, 256, 4096), 256, 0, s>>>(hkeys, nh, g->bitsN, heavy);
+      count_launch();
+      if ((st = dalloc_t(&dmx, 1, s)) != PB_OK) break;
+      if (cudaMemsetAsync(dmx, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, g->wpre, n, dmx);
+      count_launch();
+      unsigned long long hdm = 0;
+      if (cudaMemcpyAsync(&hdm, dmx, sizeof(hdm), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "heavy readback"); break; }
+      HeavySlots hs = {};
+      hs.n = n;
+      size_t slot_bytes;
+      if (p.dense) {
+        hs.tcap = hdm < n ? hdm : n;
+        slot_bytes = (hs.n + hs.tcap) * sizeof(uint32_t);
+      } else {
+        uint64_t cap = 32;
+        while (cap < 2 * hdm) cap <<= 1;
+        hs.hcap = cap;
+        slot_bytes = 2 * cap * sizeof(uint32_t);
+      }
+      unsigned cl = p.cluster;
+      auto kern = p.dense ? k_heavy<PV, PE, true> : k_heavy<PV, PE, false>;
+      int nc = max_clusters(kern, HB_THREADS, cl);
+      if (nc <= 0) nc = sms / static_cast<int>(cl);
+      uint64_t fit = budget / (slot_bytes + 16);
+      if (fit == 0) { st = fail(PB_ERR_SCRATCH, "scratch budget %llu B below one heavy slot (%llu B)", (unsigned long long)budget, (unsigned long long)slot_bytes); break; }
+      uint64_t nslots = static_cast<uint64_t>(nc);
+      if (nslots > fit) nslots = fit;
+      if (nslots > nh) nslots = nh;
+      size_t need = nslots * slot_bytes + nslots * 3 * sizeof(uint32_t) + 64;
+      if ((st = ensure_scratch(g, need, s)) != PB_OK) break;
+      char *sp = static_cast<char *>(g->scratch);
+      if (p.dense) {
+        hs.A = reinterpret_cast<uint32_t *>(sp);
+        hs.T = hs.A + nslots * hs.n;
+        hs.tcnt = hs.T + nslots * hs.tcap;
+        if (cudaMemsetAsync(hs.A, 0, nslots * hs.n * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      } else {
+        hs.hkey = reinterpret_cast<uint32_t *>(sp);
+        hs.hval = hs.hkey + nslots * hs.hcap;
+        hs.tcnt = hs.hval + nslots * hs.hcap;
+        if (cudaMemsetAsync(hs.hkey, 0xff, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess ||
+            cudaMemsetAsync(hs.hval, 0, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      }
+      hs.item = hs.tcnt + 2 * nslots;
+      if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, s, a,
+                               (const uint32_t *)heavy, nh, hs)) != PB_OK) break;
+    }
+  } while (0);
+  dfree(light, s); dfree(med, s); dfree(heavy, s); dfree(hkeys, s); dfree(dmx, s);
+  return st;
+}
+
+template <bool PV, bool PE>
+static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, cudaStream_t s) {
+  const uint64_t n = g->n;
+  const int bitsN = g->bitsN;
+  // bytes per wedge: key, radix ping-pong key, head, run id, run key, run start, run d
+  const uint64_t per_wedge = 8 + 8 + 4 + 4 + 8 + 4 + 4;
+  uint64_t cap = budget / per_wedge;
+  if (cap > (uint64_t(1) << 31)) cap = uint64_t(1) << 31;
+  if (cap < g->maxw) return fail(PB_ERR_SCRATCH, "sort aggregation: one first endpoint has %llu wedges, budget holds %llu",
+                                 (unsigned long long)g->maxw, (unsigned long long)cap);
+  unsigned long long *dchunk = nullptr;
+  uint64_t *keys = nullptr, *ukey = nullptr;
+  uint32_t *head = nullptr, *cid = nullptr, *rstart = nullptr, *ud = nullptr, *seg = nullptr;
+  pb_status st = PB_OK;
+  uint64_t cap_alloc = cap < g->W ? cap : g->W;
+  if (cap_alloc == 0) return PB_OK;
+  do {
+    if ((st = dalloc_t(&dchunk, 2, s)) != PB_OK) break;
+    if ((st = dalloc_t(&keys, cap_alloc, s)) != PB_OK) break;
+    if ((st = dalloc_t(&head, cap_alloc, s)) != PB_OK) break;
+    if ((st = dalloc_t(&cid, cap_alloc + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&ukey, cap_alloc, s)) != PB_OK) break;
+    if ((st = dalloc_t(&rstart, cap_alloc, s)) != PB_OK) break;
+    if ((st = dalloc_t(&ud, cap_alloc, s)) != PB_OK) break;
+    const int sms = sm_count(g->device);
+    uint32_t lo = 0;
+    while (lo < n && st == PB_OK) {
+      k_chunk_end<<<1, 1, 0, s>>>(g->wpre, n, lo, cap, dchunk);
+      count_launch();
+      unsigned long long hc[2];
+      if (cudaMemcpyAsync(hc, dchunk, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "chunk readback"); break; }
+      const uint32_t hi = static_cast<uint32_t>(hc[0]);
+      const uint64_t cnt = hc[1];
+      if (cnt > 0) {
+        uint64_t wbase = 0;
+        if (cudaMemcpyAsync(&wbase, g->wpre + lo, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
+        cudaStreamSynchronize(s);
+        if (cudaMemsetAsync(a.acc + ACC_QMED, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        unsigned grid = static_cast<unsigned>(sms * 4);
+        if (grid > hi - lo) grid = hi - lo;
+        k_sort_walk<PV, PE, true><<<grid, MB_THREADS, 0, s>>>(a, lo, hi, wbase, bitsN, keys, nullptr, nullptr, nullptr);
+        count_launch();
+        int kbits = bits_for(hi - lo - 1) + bitsN;
+        if ((st = radix_sort(keys, nullptr, cnt, kbits, s)) != PB_OK) break;
+        k_heads<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(keys, cnt, head);
+        count_launch();
+        if ((st = scan_u32(head, cid, cnt, s)) != PB_OK) break;
+        uint32_t nr = 0;
+        if (cudaMemcpyAsync(&nr, cid + cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "run count readback"); break; }
+        k_runs<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(keys, head, cid, cnt, ukey, rstart);
+        count_launch();
+        k_run_sums<PV><<<grid_for(nr, 256, 4096), 256, 0, s>>>(a, ukey, rstart, nr, static_cast<uint32_t>(cnt), lo,
+                                                               bitsN, ud);
+        count_launch();
+        if (PV || PE) {
+          dfree(seg, s);
+          seg = nullptr;
+          if ((st = dalloc_t(&seg, (hi - lo) + 1, s)) != PB_OK) break;
+          k_segments<<<grid_for(hi - lo + 1, 256, 4096), 256, 0, s>>>(ukey, nr, hi - lo, bitsN, seg);
+          count_launch();
+          if (cudaMemsetAsync(a.acc + ACC_QMED, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+          k_sort_walk<PV, PE, false><<<grid, MB_THREADS, 0, s>>>(a, lo, hi, wbase, bitsN, nullptr, ukey, ud, seg);
+          count_launch();
+        }
+        if (cudaGetLastError() != cudaSuccess) { st = fail(PB_ERR_CUDA, "sort aggregation kernels failed to launch"); break; }
+      }
+      lo = hi;
+    }
+  } while (0);
+  dfree(dchunk, s); dfree(keys, s); dfree(head, s); dfree(cid, s); dfree(ukey, s); dfree(rstart, s);
+  dfree(ud, s); dfree(seg, s);
+  return st;
+}
+
+pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut &o, cudaStream_t s) {
+  if (g->rank_kind < 0) PB_TRY(rank_graph(g, PB_RANK_SIDE, nullptr, 0, s));
+  if (agg < 0 || agg > PB_AGG_AUTO) return fail(PB_ERR_INVALID, "unknown aggregation %d", agg);
+  const uint64_t n = g->n, na = 2 * g->m;
+  const bool want_pv = o.U || o.V, want_pe = o.E != nullptr;
+  uint64_t budget = scratch_bytes ? scratch_bytes : (uint64_t(16) << 30);
+  if (!g->acc) PB_CUDA(cudaMalloc(&g->acc, ACC_WORDS * sizeof(unsigned long long)));
+  PB_CUDA(cudaMemsetAsync(g->acc, 0, ACC_WORDS * sizeof(unsigned long long), s));
+  if (want_pv) {
+    if (!g->pv) PB_CUDA(cudaMalloc(&g->pv, (n + 1) * sizeof(uint64_t)));
+    PB_CUDA(cudaMemsetAsync(g->pv, 0, (n + 1) * sizeof(uint64_t), s));
+  }
+  if (want_pe) {
+    if (!g->es) PB_CUDA(cudaMalloc(&g->es, (na + 1) * sizeof(uint64_t)));
+    PB_CUDA(cudaMemsetAsync(g->es, 0, (na + 1) * sizeof(uint64_t), s));
+  }
+  CArgs a;
+  a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.wpre = g->wpre; a.n = n;
+  a.pv = want_pv ? reinterpret_cast<unsigned long long *>(g->pv) : nullptr;
+  a.es = want_pe ? reinterpret_cast<unsigned long long *>(g->es) : nullptr;
+  a.acc = g->acc;
+  if (g->W > 0) {
+    Plan p;
+    p.agg = agg;
+    p.pv = want_pv;
+    p.pe = want_pe;
+    p.light_max = LIGHT_MAX;
+    p.med_max = MED_MAX;
+    p.dense = agg != PB_AGG_HASH;
+    p.cluster = 4;
+    if (agg == PB_AGG_BATCH) {
+      p.med_max = LIGHT_MAX;  // everything above the light tier uses dense arrays
+      p.cluster = 1;
+    }
+    pb_status st;
+    if (agg == PB_AGG_SORT) {
+      if (want_pv && want_pe) st = run_sort<true, true>(g, a, budget, s);
+      else if (want_pv) st = run_sort<true, false>(g, a, budget, s);
+      else if (want_pe) st = run_sort<false, true>(g, a, budget, s);
+      else st = run_sort<false, false>(g, a, budget, s);
+    } else if (want_pv && want_pe) st = run_tiers<true, true>(g, a, p, budget, s);
+    else if (want_pv) st = run_tiers<true, false>(g, a, p, budget, s);
+    else if (want_pe) st = run_tiers<false, true>(g, a, p, budget, s);
+    else st = run_tiers<false, false>(g, a, p, budget, s);
+    PB_TRY(st);
+  }
+  unsigned long long hacc[ACC_WORDS] = {0};
+  PB_CUDA(cudaMemcpyAsync(hacc, g->acc, sizeof(hacc), cudaMemcpyDeviceToHost, s));
+  // outputs
+  uint64_t *dU = o.U, *dV = o.V, *dE = o.E, *tmp = nullptr;
+  if (!o.on_device && (want_pv || want_pe)) {
+    size_t cnt = (want_pv ? n : 0) + (want_pe ? g->m_in : 0);
+    PB_TRY(dalloc_t(&tmp, cnt + 1, s));
+    uint64_t *q = tmp;
+    if (want_pv) { dU = o.U ? q : nullptr; dV = o.V ? q + g->nU : nullptr; q += n; }
+    if (want_pe) dE = q;
+  }
+  pb_status st = PB_OK;
+  if (want_pv && n) {
+    k_out_vertex<<<grid_for(n, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->pv), g->rank,
+                                                         g->nU, g->nV, dU, dV);
+    count_launch();
+  }
+  if (want_pe && g->m_in) {
+    k_out_edge<<<grid_for(g->m_in, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->es),
+                                                             g->slotA, g->slotB, g->in2c, g->m_in, dE);
+    count_launch();
+  }
+  if (cudaGetLastError() != cudaSuccess) st = fail(PB_ERR_CUDA, "output kernels failed to launch");
+  if (st == PB_OK && !o.on_device) {
+    cudaError_t e = cudaSuccess;
+    if (o.U && n) e = cudaMemcpyAsync(o.U, dU, g->nU * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && o.V && n) e = cudaMemcpyAsync(o.V, dV, g->nV * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && o.E && g->m_in) e = cudaMemcpyAsync(o.E, dE, g->m_in * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "output download", __FILE__, __LINE__);
+  }
+  dfree(tmp, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st != PB_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "counting kernels", __FILE__, __LINE__);
+  if (hacc[ACC_ERR]) return fail(PB_ERR_SCRATCH, "aggregation table overflow (code %llu)", hacc[ACC_ERR]);
+  if (hacc[ACC_OVF]) return fail(PB_ERR_OVERFLOW, "global butterfly count exceeds 2^64");
+  if (o.global) *o.global = hacc[0];
+  return PB_OK;
+}
+
+}  // namespace pb

@@ -1,0 +1,444 @@
+// Graph construction (bipartite CSR input, duplicate removal) and PREPROCESS
+// (Algorithm 1): rank keys, device radix sorts, renaming, adjacency sorted by
+// decreasing rank, the modified degrees deg_x(y), and the per-first-endpoint
+// wedge counts with their prefix sum (the work split of Algorithm 2).
+#include "pb_common.cuh"
+
+namespace pb {
+
+// ---------------------------------------------------------------------------
+// Input validation and duplicate removal.
+
+__global__ void k_validate(const uint32_t *__restrict__ u, const uint32_t *__restrict__ v, size_t m,
+                           uint32_t nU, uint32_t nV, unsigned long long *bad) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    if (u[i] >= nU || v[i] >= nV) atomicAdd(bad, 1ull);
+}
+
+__global__ void k_pair_keys(const uint32_t *__restrict__ u, const uint32_t *__restrict__ v, size_t m,
+                            int bitsV, uint64_t *__restrict__ keys, uint32_t *__restrict__ idx) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    keys[i] = (static_cast<uint64_t>(u[i]) << bitsV) | v[i];
+    idx[i] = static_cast<uint32_t>(i);
+  }
+}
+
+__global__ void k_heads(const uint64_t *__restrict__ keys, size_t m, uint32_t *__restrict__ head) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_canon(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx,
+                        const uint32_t *__restrict__ head, const uint32_t *__restrict__ cid, size_t m,
+                        int bitsV, uint32_t nU, uint32_t *__restrict__ in2c, uint32_t *__restrict__ eu,
+                        uint32_t *__restrict__ ev, uint32_t *__restrict__ deg) {
+  const uint64_t maskV = (uint64_t(1) << bitsV) - 1;
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t r = cid[i] + head[i] - 1;
+    in2c[idx[i]] = r;
+    if (head[i]) {
+      uint32_t a = static_cast<uint32_t>(keys[i] >> bitsV), b = static_cast<uint32_t>(keys[i] & maskV);
+      eu[r] = a;
+      ev[r] = b;
+      atomicAdd(&deg[a], 1u);
+      atomicAdd(&deg[nU + b], 1u);
+    }
+  }
+}
+
+__global__ void k_maxdeg(const uint32_t *__restrict__ deg, uint64_t n, uint32_t nU, uint32_t *out2) {
+  uint32_t mu = 0, mv = 0;
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    if (i < nU) mu = max(mu, deg[i]);
+    else mv = max(mv, deg[i]);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mu = max(mu, __shfl_xor_sync(FULL, mu, o));
+    mv = max(mv, __shfl_xor_sync(FULL, mv, o));
+  }
+  if (lane_id() == 0) {
+    atomicMax(&out2[0], mu);
+    atomicMax(&out2[1], mv);
+  }
+}
+
+pb_status build_graph(pb_graph *g, const uint32_t *u_in, const uint32_t *v_in, int on_device,
+                      cudaStream_t s) {
+  const size_t m = g->m_in;
+  const uint64_t n = g->n;
+  PB_TRY(dalloc_t(&g->deg, n + 1, s));
+  PB_CUDA(cudaMemsetAsync(g->deg, 0, (n + 1) * sizeof(uint32_t), s));
+  PB_TRY(dalloc_t(&g->in2c, m + 1, s));
+  unsigned long long *flag = nullptr;
+  PB_TRY(dalloc_t(&flag, 2, s));
+  const uint32_t *u = u_in, *v = v_in;
+  uint32_t *du = nullptr, *dv = nullptr, *idx = nullptr, *head = nullptr, *cid = nullptr;
+  uint64_t *keys = nullptr;
+  pb_status st = PB_OK;
+  unsigned long long hbad = 0;
+  uint32_t hm = 0, hmax[2] = {0, 0};
+  uint32_t *dmax = nullptr;
+  do {
+    if (m > 0 && !on_device) {
+      if ((st = dalloc_t(&du, m, s)) != PB_OK) break;
+      if ((st = dalloc_t(&dv, m, s)) != PB_OK) break;
+      cudaError_t e = cudaMemcpyAsync(du, u_in, m * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v_in, m * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) { st = cuda_fail(e, "edge upload", __FILE__, __LINE__); break; }
+      u = du;
+      v = dv;
+    }
+    if (cudaMemsetAsync(flag, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if (m > 0) {
+      k_validate<<<grid_for(m, 256, 8192), 256, 0, s>>>(u, v, m, g->nU, g->nV, flag);
+      count_launch();
+    }
+    if (cudaMemcpyAsync(&hbad, flag, sizeof(hbad), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "validation readback failed: %s", cudaGetErrorString(cudaGetLastError())); break; }
+    if (hbad) { st = fail(PB_ERR_INVALID, "%llu edge(s) have u >= nU or v >= nV", hbad); break; }
+    if (m == 0) { g->m = 0; break; }
+    const int bitsU = bits_for(g->nU ? g->nU - 1 : 0), bitsV = bits_for(g->nV ? g->nV - 1 : 0);
+    if ((st = dalloc_t(&keys, m, s)) != PB_OK) break;
+    if ((st = dalloc_t(&idx, m, s)) != PB_OK) break;
+    k_pair_keys<<<grid_for(m, 256, 8192), 256, 0, s>>>(u, v, m, bitsV, keys, idx);
+    count_launch();
+    if ((st = radix_sort(keys, idx, m, bitsU + bitsV, s)) != PB_OK) break;
+    if ((st = dalloc_t(&head, m, s)) != PB_OK) break;
+    if ((st = dalloc_t(&cid, m + 1, s)) != PB_OK) break;
+    k_heads<<<grid_for(m, 256, 8192), 256, 0, s>>>(keys, m, head);
+    count_launch();
+    if ((st = scan_u32(head, cid, m, s)) != PB_OK) break;
+    if (cudaMemcpyAsync(&hm, cid + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "dedupe readback failed"); break; }
+    g->m = hm;
+    if (g->m >= (uint64_t(1) << 31)) { st = fail(PB_ERR_INVALID, "more than 2^31-1 distinct edges"); break; }
+    if ((st = dalloc_t(&g->eu, g->m, s)) != PB_OK) break;
+    if ((st = dalloc_t(&g->ev, g->m, s)) != PB_OK) break;
+    k_canon<<<grid_for(m, 256, 8192), 256, 0, s>>>(keys, idx, head, cid, m, bitsV, g->nU, g->in2c,
+                                                    g->eu, g->ev, g->deg);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) { st = fail(PB_ERR_CUDA, "canonical edge kernel failed"); break; }
+  } while (0);
+  if (st == PB_OK && n > 0) {
+    do {
+      if ((st = dalloc_t(&dmax, 2, s)) != PB_OK) break;
+      if (cudaMemsetAsync(dmax, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      k_maxdeg<<<grid_for(n, 256, 2048), 256, 0, s>>>(g->deg, n, g->nU, dmax);
+      count_launch();
+      if (cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "degree readback failed"); break; }
+      g->maxdegU = hmax[0];
+      g->maxdegV = hmax[1];
+    } while (0);
+  }
+  dfree(du, s); dfree(dv, s); dfree(keys, s); dfree(idx, s); dfree(head, s); dfree(cid, s);
+  dfree(flag, s); dfree(dmax, s);
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// Rank keys (Sec. "Ranking").  Sorting (class << bitsN | global id) ascending
+// gives the order; ties fall back to the global id.
+
+__global__ void k_side_wedges(const uint32_t *__restrict__ deg, uint64_t n, uint32_t nU,
+                              unsigned long long *w2) {
+  // w2[0]: wedges with endpoints in U = sum over v of C(deg v, 2)
+  // w2[1]: wedges with endpoints in V = sum over u of C(deg u, 2)
+  unsigned long long a = 0, b = 0;
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    unsigned long long d = deg[i], c = d ? d * (d - 1) / 2 : 0;
+    if (i < nU) b += c;
+    else a += c;
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane_id() == 0) {
+    if (a) atomicAdd(&w2[0], a);
+    if (b) atomicAdd(&w2[1], b);
+  }
+}
+
+__global__ void k_side_rank(uint64_t n, uint32_t nU, uint32_t nV, int u_first, uint32_t *__restrict__ rank,
+                            uint32_t *__restrict__ order) {
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t r = x < nU ? (u_first ? static_cast<uint32_t>(x) : nV + static_cast<uint32_t>(x))
+                        : (u_first ? static_cast<uint32_t>(x) : static_cast<uint32_t>(x - nU));
+    rank[x] = r;
+    order[r] = static_cast<uint32_t>(x);
+  }
+}
+
+__global__ void k_rank_keys(const uint32_t *__restrict__ deg, uint64_t n, int kind, uint32_t maxdeg,
+                            int bitsN, uint64_t *__restrict__ keys) {
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t d = deg[x];
+    uint64_t cls;
+    if (kind == PB_RANK_DEGREE) cls = maxdeg - d;                // decreasing degree
+    else cls = d == 0 ? 32u : 31u - (31u - __clz(d));            // decreasing floor(log2 d), 0 last
+    keys[x] = (cls << bitsN) | x;
+  }
+}
+
+__global__ void k_rank_from_keys(const uint64_t *__restrict__ keys, uint64_t n, int bitsN,
+                                 uint32_t *__restrict__ rank, uint32_t *__restrict__ order) {
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
+  for (size_t r = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t x = static_cast<uint32_t>(keys[r] & mask);
+    order[r] = x;
+    rank[x] = static_cast<uint32_t>(r);
+  }
+}
+
+__global__ void k_custom_rank(const uint32_t *__restrict__ rank_of, uint64_t n, uint32_t *__restrict__ rank,
+                              uint32_t *__restrict__ order, uint32_t *__restrict__ seen,
+                              unsigned long long *bad) {
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t r = rank_of[x];
+    rank[x] = r;
+    if (r >= n || atomicAdd(&seen[r], 1u) != 0) {
+      atomicAdd(bad, 1ull);
+    } else {
+      order[r] = static_cast<uint32_t>(x);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Renaming + adjacency in rank space.  Every canonical edge e = (u, v) gives
+// two arcs: 2e from rank(u) to rank(v) and 2e+1 back.  Keys (x << bitsN) |
+// (maxrank - y) sort the arcs by source, then by decreasing neighbour rank.
+
+__global__ void k_arc_keys(const uint32_t *__restrict__ eu, const uint32_t *__restrict__ ev, uint64_t m,
+                           uint32_t nU, const uint32_t *__restrict__ rank, int bitsN,
+                           uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint64_t a = rank[eu[e]], b = rank[nU + ev[e]];
+    keys[2 * e] = (a << bitsN) | (mask - b);
+    vals[2 * e] = static_cast<uint32_t>(2 * e);
+    keys[2 * e + 1] = (b << bitsN) | (mask - a);
+    vals[2 * e + 1] = static_cast<uint32_t>(2 * e + 1);
+  }
+}
+
+__global__ void k_rank_degree(const uint32_t *__restrict__ deg, const uint32_t *__restrict__ order,
+                              uint64_t n, uint32_t *__restrict__ degr) {
+  for (size_t r = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<size_t>(gridDim.x) * blockDim.x)
+    degr[r] = deg[order[r]];
+}
+
+__global__ void k_arcs_out(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint64_t na,
+                           int bitsN, uint32_t *__restrict__ adj, uint32_t *__restrict__ slotA,
+                           uint32_t *__restrict__ slotB) {
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
+  for (size_t s = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < na;
+       s += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    adj[s] = static_cast<uint32_t>(mask - (keys[s] & mask));
+    uint32_t a = vals[s];
+    if (a & 1u) slotB[a >> 1] = static_cast<uint32_t>(s);
+    else slotA[a >> 1] = static_cast<uint32_t>(s);
+  }
+}
+
+// cpos[s] = position of the list owner x in y's list (= deg_x(y), the number
+// of y's neighbours ranked above x, since lists are strictly decreasing);
+// degp[x] = deg_x(x), the length of the prefix of x's list ranked above x.
+__global__ void k_cpos_degp(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                            uint64_t na, int bitsN, const uint32_t *__restrict__ off,
+                            const uint32_t *__restrict__ adj, const uint32_t *__restrict__ slotA,
+                            const uint32_t *__restrict__ slotB, uint32_t *__restrict__ cpos,
+                            uint32_t *__restrict__ degp) {
+  for (size_t s = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < na;
+       s += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t a = vals[s];
+    uint32_t other = (a & 1u) ? slotA[a >> 1] : slotB[a >> 1];
+    uint32_t y = adj[s];
+    cpos[s] = other - off[y];
+    uint32_t x = static_cast<uint32_t>(keys[s] >> bitsN);
+    if (y > x && (s + 1 == off[x + 1] || adj[s + 1] < x)) degp[x] = static_cast<uint32_t>(s + 1 - off[x]);
+  }
+}
+
+// wedges(x) = sum over the first degp[x] slots of x of cpos; warp-aggregated.
+__global__ void k_wedges_per_x(const uint64_t *__restrict__ keys, uint64_t na, int bitsN,
+                               const uint32_t *__restrict__ off, const uint32_t *__restrict__ degp,
+                               const uint32_t *__restrict__ cpos, unsigned long long *__restrict__ wc) {
+  size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  size_t iters = (na + stride - 1) / stride;
+  for (size_t it = 0; it < iters; it++) {
+    size_t s = start + it * stride;
+    bool valid = s < na;
+    uint32_t x = valid ? static_cast<uint32_t>(keys[s] >> bitsN) : 0xffffffffu;
+    unsigned long long c = 0;
+    if (valid && s - off[x] < degp[x]) c = cpos[s];
+    uint32_t peers = __match_any_sync(FULL, x);
+    // sum c over the peer group, result in its lowest lane
+    uint32_t leader = __ffs(peers) - 1;
+    unsigned long long tot = 0;
+    for (uint32_t p = peers; p; p &= p - 1) {
+      uint32_t l = __ffs(p) - 1;
+      unsigned long long cl = __shfl_sync(peers, c, l);
+      tot += cl;
+    }
+    if (valid && lane_id() == leader && tot) atomicAdd(&wc[x], tot);
+  }
+}
+
+__global__ void k_max_u64(const unsigned long long *__restrict__ a, uint64_t n, unsigned long long *out) {
+  unsigned long long mx = 0;
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    mx = a[i] > mx ? a[i] : mx;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(FULL, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if (lane_id() == 0 && mx) atomicMax(out, mx);
+}
+
+void free_ranked(pb_graph *g) {
+  cudaFree(g->rank); cudaFree(g->order); cudaFree(g->off); cudaFree(g->adj); cudaFree(g->cpos);
+  cudaFree(g->degp); cudaFree(g->wpre); cudaFree(g->slotA); cudaFree(g->slotB);
+  g->rank = g->order = g->off = g->adj = g->cpos = g->degp = g->slotA = g->slotB = nullptr;
+  g->wpre = nullptr;
+  g->rank_kind = -1;
+  g->W = g->maxw = 0;
+}
+
+static pb_status alloc_ranked(pb_graph *g) {
+  const uint64_t n = g->n, na = 2 * g->m;
+  PB_CUDA(cudaMalloc(&g->rank, (n + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->order, (n + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->adj, (na + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->cpos, (na + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->degp, (n + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->wpre, (n + 1) * sizeof(uint64_t)));
+  PB_CUDA(cudaMalloc(&g->slotA, (g->m + 1) * sizeof(uint32_t)));
+  PB_CUDA(cudaMalloc(&g->slotB, (g->m + 1) * sizeof(uint32_t)));
+  return PB_OK;
+}
+
+pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_device, cudaStream_t s) {
+  free_ranked(g);
+  const uint64_t n = g->n, m = g->m, na = 2 * m;
+  const int bitsN = g->bitsN;
+  pb_status st = alloc_ranked(g);
+  if (st != PB_OK) { free_ranked(g); return st; }
+  uint64_t *keys = nullptr;
+  uint32_t *vals = nullptr, *tmp = nullptr, *drank = nullptr;
+  unsigned long long *acc = nullptr, *wc = nullptr;
+  unsigned long long hacc[2] = {0, 0};
+  do {
+    if ((st = dalloc_t(&acc, 2, s)) != PB_OK) break;
+    if (cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    // ---- 1. the ranking
+    if (rank_of) {
+      const uint32_t *src = rank_of;
+      if (!on_device) {
+        if ((st = dalloc_t(&drank, n + 1, s)) != PB_OK) break;
+        if (cudaMemcpyAsync(drank, rank_of, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "rank upload"); break; }
+        src = drank;
+      }
+      if ((st = dalloc_t(&tmp, n + 1, s)) != PB_OK) break;
+      if (cudaMemsetAsync(tmp, 0, (n + 1) * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      if (n) {
+        k_custom_rank<<<grid_for(n, 256, 8192), 256, 0, s>>>(src, n, g->rank, g->order, tmp, acc);
+        count_launch();
+      }
+      if (cudaMemcpyAsync(hacc, acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "rank check readback"); break; }
+      if (hacc[0]) { st = fail(PB_ERR_INVALID, "rank_of is not a permutation of [0, %llu)", (unsigned long long)n); break; }
+      dfree(tmp, s);
+      tmp = nullptr;
+    } else if (kind == PB_RANK_SIDE) {
+      if (n) {
+        k_side_wedges<<<grid_for(n, 256, 2048), 256, 0, s>>>(g->deg, n, g->nU, acc);
+        count_launch();
+      }
+      if (cudaMemcpyAsync(hacc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "side wedge readback"); break; }
+      int u_first = hacc[0] <= hacc[1];
+      if (n) {
+        k_side_rank<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, g->nU, g->nV, u_first, g->rank, g->order);
+        count_launch();
+      }
+    } else {
+      uint32_t maxdeg = g->maxdegU > g->maxdegV ? g->maxdegU : g->maxdegV;
+      int cbits = kind == PB_RANK_DEGREE ? bits_for(maxdeg) : 6;
+      if ((st = dalloc_t(&keys, n + 1, s)) != PB_OK) break;
+      if (n) {
+        k_rank_keys<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->deg, n, kind, maxdeg, bitsN, keys);
+        count_launch();
+      }
+      if ((st = radix_sort(keys, nullptr, n, bitsN + cbits, s)) != PB_OK) break;
+      if (n) {
+        k_rank_from_keys<<<grid_for(n, 256, 8192), 256, 0, s>>>(keys, n, bitsN, g->rank, g->order);
+        count_launch();
+      }
+      dfree(keys, s);
+      keys = nullptr;
+    }
+    // ---- 2. offsets in rank space
+    if ((st = dalloc_t(&tmp, n + 1, s)) != PB_OK) break;
+    if (n) {
+      k_rank_degree<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->deg, g->order, n, tmp);
+      count_launch();
+    }
+    if ((st = scan_u32(tmp, g->off, n, s)) != PB_OK) break;
+    dfree(tmp, s);
+    tmp = nullptr;
+    if (cudaMemsetAsync(g->degp, 0, (n + 1) * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if ((st = dalloc_t(&wc, n + 1, s)) != PB_OK) break;
+    if (cudaMemsetAsync(wc, 0, (n + 1) * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if (na > 0) {
+      // ---- 3. arcs sorted by (source, decreasing neighbour)
+      if ((st = dalloc_t(&keys, na, s)) != PB_OK) break;
+      if ((st = dalloc_t(&vals, na, s)) != PB_OK) break;
+      k_arc_keys<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, g->rank, bitsN, keys, vals);
+      count_launch();
+      if ((st = radix_sort(keys, vals, na, 2 * bitsN, s)) != PB_OK) break;
+      k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->adj, g->slotA, g->slotB);
+      count_launch();
+      k_cpos_degp<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->off, g->adj, g->slotA,
+                                                           g->slotB, g->cpos, g->degp);
+      count_launch();
+      // ---- 4. wedges per first endpoint and the work split prefix
+      k_wedges_per_x<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, na, bitsN, g->off, g->degp, g->cpos, wc);
+      count_launch();
+    }
+    if ((st = scan_u64(reinterpret_cast<uint64_t *>(wc), g->wpre, n, s)) != PB_OK) break;
+    if (cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if (n) {
+      k_max_u64<<<grid_for(n, 256, 2048), 256, 0, s>>>(wc, n, acc);
+      count_launch();
+    }
+    uint64_t hW = 0;
+    if (cudaMemcpyAsync(&hW, g->wpre + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hacc, acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "wedge count readback: %s", cudaGetErrorString(cudaGetLastError())); break; }
+    g->W = hW;
+    g->maxw = hacc[0];
+    g->rank_kind = rank_of ? 3 : kind;
+  } while (0);
+  dfree(keys, s); dfree(vals, s); dfree(tmp, s); dfree(drank, s); dfree(acc, s); dfree(wc, s);
+  if (st != PB_OK) free_ranked(g);
+  return st;
+}
+
+}  // namespace pb
