@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: exact butterfly counting on one GB300 (or N replicas).
+
+One step = the whole counting path over one synthetic graph:
+  pb_graph_from_edges (device-resident edge list: dedupe + CSR)
+  -> pb_rank (PREPROCESS: ranking, relabelling, adjacency by decreasing rank,
+     deg_x(y), wedge work split)
+  -> pb_count_all (wedge retrieval + aggregation; global, per-vertex and
+     per-edge counts in one pass)
+Metric: wedges aggregated per second, W / step time, where W is the exact
+number of wedges the ranking retrieves (Algorithm 2).  Counts are exact uint64.
+
+Default workload: Chung-Lu bipartite graph |U|=1M, |V|=4M, m=50M distinct
+edges, expected-degree exponents 2.1 (U) / 2.5 (V), expected degree capped at
+1e5, degree ranking, automatic aggregation.
+
+Multi-GPU (torchrun): every rank counts its own replica of the workload (the
+path has no exchange step), so per-GPU work is fixed: weak scaling, value =
+N * W / max-over-ranks time.
+
+--impl reference times the CPU oracle (the plain implementation the tests
+check against) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wedges aggregated/sec and % HBM roofline, exact counts; batched/served p50/p99 vs plain"
+UNIT = "wedges/s"
+
+WORKLOADS = {
+    "er1": dict(desc="ER |U|=2000 |V|=3000 m=2e4", idx=1),
+    "cl2": dict(desc="Chung-Lu |U|=1M |V|=4M m=5e7, exponents 2.1/2.5, cap 1e5", idx=2),
+    "cl3": dict(desc="Chung-Lu |U|=20M |V|=60M m=3e8, exponents 2.0/2.0, cap 1e5", idx=3),
+    # quarter-scale copy of cl2 for profiler captures (a few GB on the device)
+    "cl2s": dict(desc="Chung-Lu |U|=250k |V|=1M m=1.25e7, exponents 2.1/2.5, cap 1e5", idx=-2),
+}
+# Bounded CPU sample of each workload for the oracle: the same generator
+# recipe at a reduced scale.
+SAMPLES = {
+    "er1": dict(kind="er", nU=2000, nV=3000, m=20000),
+    "cl2": dict(kind="cl", nU=200_000, nV=800_000, m=10_000_000, gu=2.1, gv=2.5, cap=1e5),
+    "cl3": dict(kind="cl", nU=800_000, nV=2_400_000, m=12_000_000, gu=2.0, gv=2.0, cap=1e5),
+    "cl2s": dict(kind="cl", nU=200_000, nV=800_000, m=10_000_000, gu=2.1, gv=2.5, cap=1e5),
+}
+
+# Algorithmic bytes per wedge of a pass producing global, per-vertex and
+# per-edge counts: 4 B to read the second endpoint, and an 8 B read + 8 B write
+# of the per-edge counter it updates ("streaming, no reuse" model).
+BYTES_PER_WEDGE = {"all": 20, "global": 4, "vertex": 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cl2", choices=sorted(WORKLOADS))
+    ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree"])
+    ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool = True):
+        self.index, self.enabled, self.proc, self.lines = index, enabled, None, []
+
+    def __enter__(self):
+        if self.enabled:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                     "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.t = threading.Thread(target=self._read, daemon=True)
+                self.t.start()
+            except OSError:
+                self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(workload: str, nthreads: int | None = None) -> dict:
+    """The oracle as it stands, on a bounded sample of the workload."""
+    import oracle
+    import synth
+    sp = SAMPLES[workload]
+    seed = synth.SEED_BASE + 100 + WORKLOADS[workload]["idx"]
+    if sp["kind"] == "er":
+        g = synth.er_graph(seed, sp["nU"], sp["nV"], sp["m"])
+    else:
+        g = synth.chung_lu_graph(seed, sp["nU"], sp["nV"], sp["m"], sp["gu"], sp["gv"], cap_u=sp["cap"],
+                                 cap_v=sp["cap"])
+    threads = nthreads or oracle.threads()
+    t0 = time.perf_counter()
+    c = oracle.count(g.nU, g.nV, g.u, g.v, kind="degree", per_vertex=True, per_edge=True, nthreads=threads)
+    dt = time.perf_counter() - t0
+    desc = (f"{sp['kind']} |U|={sp['nU']} |V|={sp['nV']} m={sp['m']} (same recipe, reduced scale), degree "
+            f"ranking, global+per-vertex+per-edge, dedupe+preprocess+count timed")
+    return {"value": c.W / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+            "seconds": dt, "W": c.W}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(args.workload)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": r["sample"], "rank": "degree"},
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1907_08607_gb300 as pb
+    from paper_1907_08607_gb300 import build as pbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    pbuild.build()
+    pb.load_library()
+
+    # CPU baseline first (host threads only, before heavy GPU work).
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    g = synth.workload(WORKLOADS[args.workload]["idx"])
+    du = torch.from_numpy(g.u.view(np.int32)).to(dev)
+    dv = torch.from_numpy(g.v.view(np.int32)).to(dev)
+    outs = {"U": torch.empty(g.nU, dtype=torch.int64, device=dev),
+            "V": torch.empty(g.nV, dtype=torch.int64, device=dev),
+            "E": torch.empty(g.m, dtype=torch.int64, device=dev)}
+    stream = torch.cuda.current_stream()
+
+    state = {}
+
+    def step():
+        G = pb.Graph.from_edges(g.nU, g.nV, du, dv)
+        G.rank(args.rank)
+        c = G.count_all(args.agg, on_device=True, out=outs)
+        state["W"] = G.wedges
+        state["global"] = c.global_count
+        G.free()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    pb.profile(enable=True, reset=True)
+    l0 = pb.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev, enabled=not args.no_clocks) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = pb.kernel_launches() - l0
+    prof = pb.profile(enable=False)
+    if dist is not None:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    W = state["W"]
+    value = world * W / (ms_step / 1e3)
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.from_numpy(g.u.view(np.int32)).pin_memory()
+        hv = torch.from_numpy(g.v.view(np.int32)).pin_memory()
+        hout = {"U": torch.empty(g.nU, dtype=torch.int64).pin_memory(),
+                "V": torch.empty(g.nV, dtype=torch.int64).pin_memory(),
+                "E": torch.empty(g.m, dtype=torch.int64).pin_memory()}
+
+        def step_host():
+            G = pb.Graph.from_edges(g.nU, g.nV, hu, hv)
+            G.rank(args.rank)
+            G.count_all(args.agg, on_device=False, out=hout)
+            G.free()
+
+        step_host()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * W / (ems / args.steps / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * g.m, "d2h_bytes_per_step": 8 * (g.nU + g.nV + g.m) + 8,
+               "ms_per_step": ems / args.steps}
+
+    # ---- roofline of the dominant kernel (CUDA events inside the library)
+    kern = max(["light", "medium", "heavy", "sort"], key=lambda k: prof[k]["ms"])
+    kp = prof[kern]
+    peak, peak_src = measured_peaks()
+    roof = None
+    if kp["records"] > 0 and kp["ms"] > 0:
+        per_launch_ms = kp["ms"] / kp["records"]
+        per_launch_bytes = BYTES_PER_WEDGE["all"] * kp["wedges"] / kp["records"]
+        achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": kern, "peak_source": peak_src,
+                "launch_ms": per_launch_ms, "algorithmic_bytes_per_launch": per_launch_bytes}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    clocks = clk.summary() if not args.no_clocks else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "rank": args.rank, "agg": args.agg,
+                   "outputs": "global+per-vertex+per-edge", "W": W, "butterflies": state["global"],
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (400 MB edge list)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["records"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

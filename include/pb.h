@@ -163,6 +163,33 @@ pb_status pb_graph_free(pb_graph *g);
  * graphs, all devices); used to report launch counts. */
 uint64_t pb_kernel_launches(void);
 
+/* Phase profiling (process-wide).  While enabled, every call records CUDA
+ * events on its stream around each phase below and accumulates the elapsed
+ * device time, the kernel launches and the wedges the phase processed.
+ * Recording adds two events per phase and nothing else; results are exact
+ * either way. */
+enum {
+  PB_PHASE_BUILD = 0,    /* pb_graph_from_edges: upload, validation, dedupe */
+  PB_PHASE_RANK = 1,     /* PREPROCESS: rank, relabel, adjacency, work split */
+  PB_PHASE_CLASSIFY = 2, /* binning first endpoints by wedge count */
+  PB_PHASE_LIGHT = 3,    /* warp-per-endpoint shared-memory hash kernel */
+  PB_PHASE_MEDIUM = 4,   /* block-per-endpoint shared-memory hash kernel */
+  PB_PHASE_HEAVY = 5,    /* cluster-per-endpoint device-memory kernel */
+  PB_PHASE_SORT = 6,     /* sort aggregation (all its kernels) */
+  PB_PHASE_OUTPUT = 7,   /* rank space -> id space / input order, downloads */
+  PB_NPHASE = 8
+};
+typedef struct {
+  double ms[PB_NPHASE];         /* accumulated device time */
+  uint64_t launches[PB_NPHASE]; /* kernels launched */
+  uint64_t wedges[PB_NPHASE];   /* wedges aggregated (counting phases) */
+  uint64_t records[PB_NPHASE];  /* phase executions */
+} pb_profile_t;
+
+void pb_profile_enable(int on);
+void pb_profile_reset(void);
+pb_status pb_profile_read(pb_profile_t *out);
+
 const char *pb_last_error(void);
 const char *pb_status_string(pb_status s);
 

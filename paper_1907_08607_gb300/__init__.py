@@ -32,7 +32,10 @@ STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 
 # Every function the C ABI exports (include/pb.h).
 ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ranks", "pb_count_global",
                "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
-               "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string"]
+               "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string",
+               "pb_profile_enable", "pb_profile_reset", "pb_profile_read"]
+
+PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
 _lock = threading.Lock()
 _lib = None
@@ -49,6 +52,15 @@ class GraphInfo(ctypes.Structure):
                 ("m", ctypes.c_uint64), ("max_deg_U", ctypes.c_uint32), ("max_deg_V", ctypes.c_uint32),
                 ("rank_kind", ctypes.c_int32), ("W", ctypes.c_uint64), ("max_wedges_x1", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8),
+                ("wedges", ctypes.c_uint64 * 8), ("records", ctypes.c_uint64 * 8)]
+
+    def as_dict(self):
+        return {ph: dict(ms=self.ms[i], launches=int(self.launches[i]), wedges=int(self.wedges[i]),
+                         records=int(self.records[i])) for i, ph in enumerate(PHASES)}
 
 
 def load_library(path: str = LIB_PATH):
@@ -83,6 +95,12 @@ def load_library(path: str = LIB_PATH):
         lib.pb_last_error.restype = ctypes.c_char_p
         lib.pb_status_string.argtypes = [i32]
         lib.pb_status_string.restype = ctypes.c_char_p
+        lib.pb_profile_enable.argtypes = [i32]
+        lib.pb_profile_enable.restype = None
+        lib.pb_profile_reset.argtypes = []
+        lib.pb_profile_reset.restype = None
+        lib.pb_profile_read.argtypes = [ctypes.POINTER(Profile)]
+        lib.pb_profile_read.restype = i32
         _lib = lib
         return lib
 
@@ -95,6 +113,19 @@ def _check(rc: int):
 
 def kernel_launches() -> int:
     return int(load_library().pb_kernel_launches())
+
+
+def profile(enable: bool | None = None, reset: bool = False) -> dict:
+    """Per-phase device time / launches / wedges recorded by the library
+    (CUDA events on the calling stream), optionally toggling recording."""
+    lib = load_library()
+    if reset:
+        lib.pb_profile_reset()
+    if enable is not None:
+        lib.pb_profile_enable(int(enable))
+    p = Profile()
+    _check(lib.pb_profile_read(ctypes.byref(p)))
+    return p.as_dict()
 
 
 def _torch():
@@ -237,7 +268,13 @@ class Graph:
                 V = out.get("V", np.empty(self.nV, np.uint64))
             if edge:
                 E = out.get("E", np.empty(self.m_in, np.uint64))
-            ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+
+            def ptr(a):
+                if a is None:
+                    return None
+                if isinstance(a, torch.Tensor):   # e.g. pinned host buffers
+                    return ctypes.c_void_p(a.data_ptr())
+                return ctypes.c_void_p(a.ctypes.data)
         _check(lib.pb_count_all(self._h, AGGS[agg], scratch_bytes, ctypes.byref(g) if g is not None else None,
                                 ptr(U), ptr(V), ptr(E), int(on_device), _stream(stream)))
         return Counts(int(g.value) if g is not None else None, U, V, E)

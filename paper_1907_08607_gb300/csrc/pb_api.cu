@@ -1,8 +1,10 @@
 // The C ABI (include/pb.h): argument checks, device selection, memory
 // helpers, error reporting.  Every entry point returns a status; none aborts.
 #include <cstdarg>
+#include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "pb_common.cuh"
 
@@ -30,6 +32,63 @@ pb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 
 void clear_error() { t_err.clear(); }
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---- phase profiling
+static std::atomic<bool> g_prof_on{false};
+static std::mutex g_prof_mu;
+static pb_profile_t g_prof;
+struct PendingPhase {
+  int phase;
+  cudaEvent_t e0, e1;
+  uint64_t launches, wedges;
+};
+static thread_local std::vector<PendingPhase> t_pending;
+
+bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
+
+PhaseScope::PhaseScope(int ph, cudaStream_t s) : phase(ph) {
+  if (!prof_on()) return;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  launches0 = g_launches.load(std::memory_order_relaxed);
+  cudaEventRecord(e0, s);
+  active = true;
+}
+
+void PhaseScope::finish(cudaStream_t s, uint64_t wedges_processed) {
+  if (!active || done) return;
+  cudaEventRecord(e1, s);
+  t_pending.push_back({phase, e0, e1, g_launches.load(std::memory_order_relaxed) - launches0, wedges_processed});
+  e0 = e1 = nullptr;
+  done = true;
+}
+
+PhaseScope::~PhaseScope() {
+  if (active && !done) {  // abandoned (error path): drop the events
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+}
+
+void prof_flush() {
+  if (t_pending.empty()) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto &p : t_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      g_prof.ms[p.phase] += ms;
+      g_prof.launches[p.phase] += p.launches;
+      g_prof.wedges[p.phase] += p.wedges;
+      g_prof.records[p.phase] += 1;
+    }
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  cudaGetLastError();
+  t_pending.clear();
+}
 
 // Stream-ordered allocation from the device's default pool.  The pool keeps
 // freed memory (release threshold raised once per device) so repeated calls do
@@ -68,11 +127,10 @@ void dfree(void *p, cudaStream_t s) {
 
 pb_status ensure_scratch(pb_graph *g, size_t bytes, cudaStream_t s) {
   if (g->scratch_cap >= bytes) return PB_OK;
-  PB_CUDA(cudaStreamSynchronize(s));
-  if (g->scratch) cudaFree(g->scratch);
+  dfree(g->scratch, s);
   g->scratch = nullptr;
   g->scratch_cap = 0;
-  PB_CUDA(cudaMalloc(&g->scratch, bytes));
+  PB_TRY(dalloc(&g->scratch, bytes, s));
   g->scratch_cap = bytes;
   return PB_OK;
 }
@@ -92,10 +150,13 @@ static void free_graph(pb_graph *g) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(g->device);
-  cudaDeviceSynchronize();
-  free_ranked(g);
-  cudaFree(g->in2c); cudaFree(g->eu); cudaFree(g->ev); cudaFree(g->deg);
-  cudaFree(g->scratch); cudaFree(g->pv); cudaFree(g->es); cudaFree(g->acc);
+  // All work on the graph is complete (every call synchronises its stream);
+  // pool frees on the legacy stream make the memory reusable by later calls.
+  cudaStream_t s = 0;
+  free_ranked(g, s);
+  dfree(g->in2c, s); dfree(g->eu, s); dfree(g->ev, s); dfree(g->deg, s);
+  dfree(g->scratch, s); dfree(g->pv, s); dfree(g->es, s); dfree(g->acc, s);
+  cudaStreamSynchronize(s);
   cudaGetLastError();
   cudaSetDevice(cur);
   delete g;
@@ -138,6 +199,20 @@ const char *pb_status_string(pb_status s) {
 
 uint64_t pb_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+void pb_profile_enable(int on) { g_prof_on.store(on != 0); }
+
+void pb_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::memset(&g_prof, 0, sizeof g_prof);
+}
+
+pb_status pb_profile_read(pb_profile_t *out) {
+  if (!out) return fail(PB_ERR_INVALID, "out is NULL");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  *out = g_prof;
+  return PB_OK;
+}
+
 pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v,
                               int on_device, void *stream, pb_graph **out) {
   clear_error();
@@ -160,9 +235,19 @@ pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32
   g->m_in = m;
   g->bitsN = bits_for(n - 1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  pb_status st = build_graph(g, u, v, on_device, s);
-  if (st == PB_OK) st = rank_graph(g, PB_RANK_SIDE, nullptr, 0, s);
+  pb_status st;
+  {
+    PhaseScope ph(PB_PHASE_BUILD, s);
+    st = build_graph(g, u, v, on_device, s);
+    if (st == PB_OK) ph.finish(s);
+  }
+  if (st == PB_OK) {
+    PhaseScope ph(PB_PHASE_RANK, s);
+    st = rank_graph(g, PB_RANK_SIDE, nullptr, 0, s);
+    if (st == PB_OK) ph.finish(s);
+  }
   cudaError_t e = cudaStreamSynchronize(s);
+  prof_flush();
   if (st == PB_OK && e != cudaSuccess) st = cuda_fail(e, "graph build", __FILE__, __LINE__);
   if (st != PB_OK) {
     std::string keep = t_err;
@@ -180,8 +265,13 @@ pb_status pb_rank(pb_graph *g, pb_rank_kind kind, void *stream) {
   if (kind < PB_RANK_SIDE || kind > PB_RANK_APPROX_DEGREE) return fail(PB_ERR_INVALID, "unknown rank kind %d", (int)kind);
   DeviceGuard dg(g->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  PB_TRY(rank_graph(g, kind, nullptr, 0, s));
+  {
+    PhaseScope ph(PB_PHASE_RANK, s);
+    PB_TRY(rank_graph(g, kind, nullptr, 0, s));
+    ph.finish(s);
+  }
   PB_CUDA(cudaStreamSynchronize(s));
+  prof_flush();
   return PB_OK;
 }
 
@@ -190,8 +280,13 @@ pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, vo
   if (!g || !rank_of) return fail(PB_ERR_INVALID, "graph or rank_of is NULL");
   DeviceGuard dg(g->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  PB_TRY(rank_graph(g, 3, rank_of, on_device, s));
+  {
+    PhaseScope ph(PB_PHASE_RANK, s);
+    PB_TRY(rank_graph(g, 3, rank_of, on_device, s));
+    ph.finish(s);
+  }
   PB_CUDA(cudaStreamSynchronize(s));
+  prof_flush();
   return PB_OK;
 }
 
@@ -218,7 +313,9 @@ pb_status pb_count_all(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t
   o.V = out_V;
   o.E = out_E;
   o.on_device = out_on_device;
-  return count_all(g, static_cast<int>(agg), scratch_bytes, o, static_cast<cudaStream_t>(stream));
+  pb_status st = count_all(g, static_cast<int>(agg), scratch_bytes, o, static_cast<cudaStream_t>(stream));
+  prof_flush();
+  return st;
 }
 
 pb_status pb_count_global(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out, void *stream) {

@@ -26,12 +26,18 @@ struct pb_graph {
   uint32_t *ev = nullptr;    // [m] V id (0-based within V)
   uint32_t *deg = nullptr;   // [n] degree by global id
 
-  // PREPROCESS output (device).  Slot s of vertex x is off[x] + i.
+  // PREPROCESS output (device).  Vertices are renamed to "labels": U
+  // vertices get [0, nU) and V vertices [nU, n), each side in increasing rank
+  // order.  Wedge endpoints always share a side, so aggregation over second
+  // endpoints touches one side's contiguous label range; comparisons between
+  // vertices are by rank and are all folded into cpos / degp below.
+  // Slot s of vertex x is off[x] + i.
   int rank_kind = -1;
   uint32_t *rank = nullptr;   // [n] rank of global id
   uint32_t *order = nullptr;  // [n] global id at rank
-  uint32_t *off = nullptr;    // [n + 1]
-  uint32_t *adj = nullptr;    // [2m] neighbour ranks, decreasing within a list
+  uint32_t *label = nullptr;  // [n] label of global id
+  uint32_t *off = nullptr;    // [n + 1] by label
+  uint32_t *adj = nullptr;    // [2m] neighbour labels, decreasing rank within a list
   uint32_t *cpos = nullptr;   // [2m] for slot (x, y): position of x in y's list = deg_x(y)
   uint32_t *degp = nullptr;   // [n] deg_x(x): neighbours ranked above x
   uint64_t *wpre = nullptr;   // [n + 1] exclusive prefix of wedges per first endpoint
@@ -80,6 +86,21 @@ void count_launch(uint64_t k = 1);
     PB_CUDA(cudaGetLastError());                                        \
   } while (0)
 
+// ---- phase profiling (pb_api.cu) ------------------------------------------
+// PhaseScope records a start event on construction and an end event on
+// finish(); elapsed times are folded in by prof_flush() after a stream sync.
+bool prof_on();
+struct PhaseScope {
+  int phase;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  uint64_t launches0 = 0, wedges = 0;
+  bool active = false, done = false;
+  PhaseScope(int ph, cudaStream_t s);
+  void finish(cudaStream_t s, uint64_t wedges_processed = 0);
+  ~PhaseScope();
+};
+void prof_flush();  // call after the stream has been synchronised
+
 // ---- device memory --------------------------------------------------------
 pb_status dalloc(void **p, size_t bytes, cudaStream_t s);  // stream-ordered
 void dfree(void *p, cudaStream_t s);
@@ -119,7 +140,7 @@ pb_status build_graph(pb_graph *g, const uint32_t *u, const uint32_t *v, int on_
                       cudaStream_t s);
 pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_device,
                      cudaStream_t s);
-void free_ranked(pb_graph *g);
+void free_ranked(pb_graph *g, cudaStream_t s);
 struct CountOut {
   uint64_t *global = nullptr;  // host
   uint64_t *U = nullptr, *V = nullptr, *E = nullptr;

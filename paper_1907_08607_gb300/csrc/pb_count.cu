@@ -26,6 +26,8 @@
 // flattened with a prefix sum over deg_x1(y) and spread evenly over threads.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+
 #include "pb_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -39,13 +41,15 @@ struct CArgs {
   const uint32_t *__restrict__ degp;
   const uint64_t *__restrict__ wpre;
   uint64_t n;
-  unsigned long long *pv;   // [n] rank space, or null
+  uint32_t nU;              // labels [0, nU) are U vertices, [nU, n) V vertices
+  unsigned long long *pv;   // [n] by label, or null
   unsigned long long *es;   // [2m] per slot, or null
   unsigned long long *acc;  // [0] global, [1] overflow, [2..] work queues
 };
 
 enum { ACC_GLOBAL = 0, ACC_OVF = 1, ACC_QMED = 2, ACC_QHEAVY = 3, ACC_NLIGHT = 4, ACC_NMED = 5,
-       ACC_NHEAVY = 6, ACC_ERR = 7, ACC_WORDS = 8 };
+       ACC_NHEAVY = 6, ACC_ERR = 7, ACC_WLIGHT = 8, ACC_WMED = 9, ACC_WHEAVY = 10, ACC_NHUB = 11,
+       ACC_WORDS = 16 };
 
 // Probe loops are bounded by the table size; running past it (impossible at
 // load <= 1/2 unless scratch is corrupt) records an error instead of spinning.
@@ -98,8 +102,16 @@ __device__ __forceinline__ uint32_t sh_get(const uint32_t *key, const uint32_t *
   return cnt[h];
 }
 
-__device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t x1) {
-  uint64_t dmax = wc < n - 1 - x1 ? wc : n - 1 - x1;  // distinct second endpoints
+// Bound on the distinct second endpoints of x1: its wedges, and the vertices
+// of its own side ranked above it (labels above x1 up to the side's end).
+__device__ __forceinline__ uint64_t distinct_bound(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1) {
+  uint64_t side_end = x1 < nU ? nU : n;
+  uint64_t above = side_end - 1 - x1;
+  return wc < above ? wc : above;
+}
+
+__device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1) {
+  uint64_t dmax = distinct_bound(wc, n, nU, x1);
   int lg = 5;
   while ((uint64_t(1) << lg) < 2 * dmax) lg++;
   return lg;
@@ -136,7 +148,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
   for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
     const uint32_t x1 = list[it];
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = table_lg(wc, a.n, x1);
+    const int lg = table_lg(wc, a.n, a.nU, x1);
     const uint32_t cap = 1u << lg;
     for (uint32_t t = lane; t < cap; t += 32) { key[t] = EMPTY; cnt[t] = 0; }
     __syncwarp();
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
     if (it >= nlist) break;
     const uint32_t x1 = list[it];
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = table_lg(wc, a.n, x1);
+    const int lg = table_lg(wc, a.n, a.nU, x1);
     const uint32_t cap = 1u << lg;
     for (uint32_t t = tid; t < cap; t += MB_THREADS) { key[t] = EMPTY; cnt[t] = 0; }
     __syncthreads();
@@ -313,26 +325,49 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
 // ---------------------------------------------------------------------------
 // Heavy tier: one cluster per first endpoint; each cluster owns one slot of
 // device-memory scratch.  The blocks of the cluster walk the same neighbour
-// chunks and take equal shares of every chunk's wedges.  Phases are separated
-// by cluster barriers (release/acquire at cluster scope); scratch written by
-// other blocks is read through L2 (ld.global.cg).
+// chunks and take equal shares of every chunk's wedges; inside a block
+// consecutive threads take consecutive wedges and every thread keeps HB_BATCH
+// of them in flight.  Phases are separated by cluster barriers
+// (release/acquire at cluster scope); scratch written by other blocks is read
+// through L2 (ld.global.cg).  A cluster of one block is plain batching: one
+// first endpoint per block and its own dense array.
+// Dense slots are indexed by the second endpoint's offset within its side.
+constexpr int HB_BATCH = 4;
+
 struct HeavySlots {
-  uint32_t *A;        // dense: [nslots][n] counts (all zero between uses)
+  uint32_t *A;        // dense: [nslots][side] counts (all zero between uses)
   uint32_t *T;        // dense: [nslots][tcap] touched second endpoints
   uint32_t *hkey;     // hash:  [nslots][hcap] keys (EMPTY between uses)
   uint32_t *hval;     // hash:  [nslots][hcap] counts
   uint32_t *tcnt;     // [nslots][2] touched counters (alternating)
   uint32_t *item;     // [nslots] current work item of the slot
-  uint64_t n, tcap, hcap;
+  uint64_t side, tcap, hcap;
 };
+
+// Appends second endpoints seen for the first time to the touched list
+// (warp-aggregated: one counter atomic per warp).
+__device__ __forceinline__ void dense_touch(const HeavySlots &h, uint32_t *T, uint32_t *tc, uint32_t x2, bool isnew,
+                                            unsigned long long *err) {
+  uint32_t bm = __ballot_sync(FULL, isnew);
+  if (bm) {
+    uint32_t leader = __ffs(bm) - 1, b0 = 0;
+    if (lane_id() == leader) b0 = atomicAdd(tc, static_cast<uint32_t>(__popc(bm)));
+    b0 = __shfl_sync(FULL, b0, leader);
+    if (isnew) {
+      uint32_t pos = b0 + __popc(bm & lanemask_lt());
+      if (pos < h.tcap) T[pos] = x2;
+      else atomicOr(err, 16ull);
+    }
+  }
+}
 
 template <bool DENSE>
 __device__ __forceinline__ void heavy_insert(const HeavySlots &h, uint32_t slot, uint32_t *A, uint32_t *T,
-                                             uint32_t *tc, int lg, uint32_t x2, bool act,
+                                             uint32_t *tc, int lg, uint32_t x2, uint32_t base, bool act,
                                              unsigned long long *err) {
   if (DENSE) {
     bool isnew = false;
-    if (act) isnew = atomicAdd(&A[x2], 1u) == 0u;
+    if (act) isnew = atomicAdd(&A[x2 - base], 1u) == 0u;
     uint32_t bm = __ballot_sync(FULL, isnew);
     if (bm) {
       uint32_t leader = __ffs(bm) - 1, b0 = 0;
@@ -362,8 +397,8 @@ __device__ __forceinline__ void heavy_insert(const HeavySlots &h, uint32_t slot,
 
 template <bool DENSE>
 __device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot, const uint32_t *A, int lg,
-                                              uint32_t x2, unsigned long long *err) {
-  if (DENSE) return __ldcg(&A[x2]);
+                                              uint32_t x2, uint32_t base, unsigned long long *err) {
+  if (DENSE) return __ldcg(&A[x2 - base]);
   const uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
   const uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
   const uint32_t mask = (1u << lg) - 1;
@@ -386,8 +421,9 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
   __shared__ unsigned long long s_sum[HB_THREADS];
   __shared__ uint32_t s_w[33];
   __shared__ unsigned long long s_w64[33];
-  uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.n : nullptr;
+  uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.side : nullptr;
   uint32_t *T = DENSE ? h.T + static_cast<size_t>(slot) * h.tcap : nullptr;
+  unsigned long long *err = &a.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   for (uint32_t k = 0;; k++) {
@@ -398,14 +434,15 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
     uint32_t *tc = &h.tcnt[2 * slot + (k & 1)];
     if (crank == 0 && tid == 0) h.tcnt[2 * slot + ((k + 1) & 1)] = 0;
     const uint32_t x1 = list[it];
+    const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = DENSE ? 0 : table_lg(wc, a.n, x1);
-    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    const int lg = DENSE ? 0 : table_lg(wc, a.n, a.nU, x1);
+    const uint32_t xbase = a.off[x1], dp = a.degp[x1];
     // ---- aggregate
     for (uint32_t k0 = 0; k0 < dp; k0 += HB_THREADS) {
       const uint32_t i = k0 + tid;
       const bool v = i < dp;
-      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+      const uint32_t y = v ? a.adj[xbase + i] : 0, c = v ? a.cpos[xbase + i] : 0;
       uint32_t tot;
       const uint32_t incl = block_incl_scan(c, s_w, &tot);
       s_incl[tid] = incl;
@@ -414,15 +451,32 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
       __syncthreads();
       const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(tot) * crank / csize);
       const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(tot) * (crank + 1) / csize);
-      for (uint32_t wb = lo; wb < hi; wb += HB_THREADS) {
-        const uint32_t wi = wb + tid;
-        const bool act = wi < hi;
-        uint32_t x2 = 0;
-        if (act) {
-          uint32_t src = block_find(s_incl, HB_THREADS, wi);
-          x2 = a.adj[s_oy[src] + (wi - s_ex[src])];
+      // interleaved: consecutive threads take consecutive wedges (coalesced
+      // adjacency reads); HB_BATCH wedges per thread are in flight at once
+      for (uint32_t wb = lo; wb < hi; wb += HB_BATCH * HB_THREADS) {
+        uint32_t x2v[HB_BATCH];
+#pragma unroll
+        for (int q = 0; q < HB_BATCH; q++) {
+          const uint32_t wi = wb + q * HB_THREADS + tid;
+          x2v[q] = 0;
+          if (wi < hi) {
+            const uint32_t src = block_find(s_incl, HB_THREADS, wi);
+            x2v[q] = a.adj[s_oy[src] + (wi - s_ex[src])];
+          }
         }
-        heavy_insert<DENSE>(h, slot, A, T, tc, lg, x2, act, &a.acc[ACC_ERR]);
+        if (DENSE) {
+          // issue every atomic of the batch before any result is used
+          uint32_t old[HB_BATCH];
+#pragma unroll
+          for (int q = 0; q < HB_BATCH; q++)
+            old[q] = wb + q * HB_THREADS + tid < hi ? atomicAdd(&A[x2v[q] - base], 1u) : 1u;
+#pragma unroll
+          for (int q = 0; q < HB_BATCH; q++) dense_touch(h, T, tc, x2v[q], old[q] == 0u, err);
+        } else {
+#pragma unroll
+          for (int q = 0; q < HB_BATCH; q++)
+            heavy_insert<DENSE>(h, slot, A, T, tc, lg, x2v[q], base, wb + q * HB_THREADS + tid < hi, err);
+        }
       }
       __syncthreads();
     }
@@ -433,7 +487,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
       const uint32_t nt = __ldcg(tc);
       for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) {
         uint32_t x2 = __ldcg(&T[t]);
-        unsigned long long d = __ldcg(&A[x2]), b = d * (d - 1) / 2;
+        unsigned long long d = __ldcg(&A[x2 - base]), b = d * (d - 1) / 2;
         own += b;
         if (PV && b) atomicAdd(&a.pv[x2], b);
       }
@@ -460,7 +514,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
       for (uint32_t k0 = 0; k0 < dp; k0 += HB_THREADS) {
         const uint32_t i = k0 + tid;
         const bool v = i < dp;
-        const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+        const uint32_t y = v ? a.adj[xbase + i] : 0, c = v ? a.cpos[xbase + i] : 0;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(c, s_w, &tot);
         s_incl[tid] = incl;
@@ -469,14 +523,30 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
         __syncthreads();
         const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(tot) * crank / csize);
         const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(tot) * (crank + 1) / csize);
-        for (uint32_t wi = lo + tid; wi < hi; wi += HB_THREADS) {
-          uint32_t src = block_find(s_incl, HB_THREADS, wi);
-          uint32_t sl = s_oy[src] + (wi - s_ex[src]);
-          uint32_t d = heavy_get<DENSE>(h, slot, A, lg, a.adj[sl], &a.acc[ACC_ERR]);
-          if (d > 1) {
-            unsigned long long t = d - 1;
-            if (PE) atomicAdd(&a.es[sl], t);
-            atomicAdd(&s_sum[src], t);
+        for (uint32_t wb = lo; wb < hi; wb += HB_BATCH * HB_THREADS) {
+          uint32_t x2v[HB_BATCH], slv[HB_BATCH], srcv[HB_BATCH], dv[HB_BATCH];
+#pragma unroll
+          for (int q = 0; q < HB_BATCH; q++) {
+            const uint32_t wi = wb + q * HB_THREADS + tid;
+            x2v[q] = 0;
+            srcv[q] = 0;
+            slv[q] = 0;
+            if (wi < hi) {
+              srcv[q] = block_find(s_incl, HB_THREADS, wi);
+              slv[q] = s_oy[srcv[q]] + (wi - s_ex[srcv[q]]);
+              x2v[q] = a.adj[slv[q]];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < HB_BATCH; q++)
+            dv[q] = wb + q * HB_THREADS + tid < hi ? heavy_get<DENSE>(h, slot, A, lg, x2v[q], base, err) : 0;
+#pragma unroll
+          for (int q = 0; q < HB_BATCH; q++) {
+            if (dv[q] > 1) {
+              unsigned long long t = dv[q] - 1;
+              if (PE) atomicAdd(&a.es[slv[q]], t);
+              atomicAdd(&s_sum[srcv[q]], t);
+            }
           }
         }
         __syncthreads();
@@ -484,7 +554,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
           unsigned long long sm = s_sum[tid];
           if (sm) {
             if (PV) atomicAdd(&a.pv[y], sm);
-            if (PE) atomicAdd(&a.es[base + i], sm);
+            if (PE) atomicAdd(&a.es[xbase + i], sm);
             s_sum[tid] = 0;
           }
         }
@@ -495,7 +565,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
     // ---- restore the slot to all-zero / all-empty
     if (DENSE) {
       const uint32_t nt = __ldcg(tc);
-      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) A[__ldcg(&T[t])] = 0;
+      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) A[__ldcg(&T[t]) - base] = 0;
     } else {
       uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
       uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
@@ -647,7 +717,7 @@ __global__ void k_chunk_end(const uint64_t *__restrict__ wpre, uint64_t n, uint3
 // ---------------------------------------------------------------------------
 // Tier classification.
 __global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64_t light_max, uint64_t med_max,
-                           uint32_t *__restrict__ light, uint32_t *__restrict__ med,
+                           uint64_t hub_min, uint32_t *__restrict__ light, uint32_t *__restrict__ med,
                            uint64_t *__restrict__ heavy_keys, int bitsN, unsigned long long *acc) {
   size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   size_t iters = (n + stride - 1) / stride;
@@ -655,8 +725,12 @@ __global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64
     size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x + itn * stride;
     uint64_t wc = x < n ? wpre[x + 1] - wpre[x] : 0;
     int tier = wc == 0 ? 0 : (wc <= light_max ? 1 : (wc <= med_max ? 2 : 3));
+    uint32_t hubs = __popc(__ballot_sync(FULL, tier == 3 && wc > hub_min));
+    if (lane_id() == 0 && hubs) atomicAdd(&acc[ACC_NHUB], (unsigned long long)hubs);
 #pragma unroll
     for (int t = 1; t <= 3; t++) {
+      unsigned long long ws = warp_sum(static_cast<unsigned long long>(tier == t ? wc : 0));
+      if (lane_id() == 0 && ws) atomicAdd(&acc[ACC_WLIGHT + t - 1], ws);
       uint32_t bm = __ballot_sync(FULL, tier == t);
       if (!bm) continue;
       uint32_t leader = __ffs(bm) - 1;
@@ -685,12 +759,11 @@ __global__ void k_keys_low(const uint64_t *__restrict__ keys, uint32_t nk, int b
 }
 
 __global__ void k_max_wedges_list(const uint32_t *__restrict__ list, uint32_t nl, const uint64_t *__restrict__ wpre,
-                                  uint64_t n, unsigned long long *out) {
+                                  uint64_t n, uint32_t nU, unsigned long long *out) {
   unsigned long long mx = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
     uint32_t x = list[i];
-    unsigned long long wc = wpre[x + 1] - wpre[x];
-    unsigned long long dm = wc < n - 1 - x ? wc : n - 1 - x;
+    unsigned long long dm = distinct_bound(wpre[x + 1] - wpre[x], n, nU, x);
     mx = dm > mx ? dm : mx;
   }
 #pragma unroll
@@ -703,12 +776,12 @@ __global__ void k_max_wedges_list(const uint32_t *__restrict__ list, uint32_t nl
 
 // ---------------------------------------------------------------------------
 // Outputs back in id space / input order.
-__global__ void k_out_vertex(const unsigned long long *__restrict__ pv, const uint32_t *__restrict__ rank,
+__global__ void k_out_vertex(const unsigned long long *__restrict__ pv, const uint32_t *__restrict__ label,
                              uint32_t nU, uint32_t nV, uint64_t *__restrict__ outU, uint64_t *__restrict__ outV) {
   const uint64_t n = static_cast<uint64_t>(nU) + nV;
   for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
        x += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint64_t c = pv[rank[x]];
+    uint64_t c = pv[label[x]];
     if (x < nU) {
       if (outU) outU[x] = c;
     } else if (outV) {
@@ -774,9 +847,18 @@ struct Plan {
   int agg;
   bool pv, pe;
   uint64_t light_max, med_max;
-  bool dense;       // heavy tier uses dense histograms
-  unsigned cluster; // blocks per heavy first endpoint
+  bool dense;         // heavy tier uses dense histograms
+  unsigned cluster;   // blocks per heavy first endpoint
+  uint64_t max_slots; // cap on concurrently processed hubs (0 = resident clusters)
+  uint64_t hub_min;   // heavy first endpoints above this many wedges get a cluster each
 };
+
+// Tuning knobs (environment): PB_HEAVY_CLUSTER, PB_HEAVY_SLOTS, PB_HUB_MIN.
+static uint64_t env_u64(const char *name, uint64_t dflt) {
+  const char *v = getenv(name);
+  if (!v || !*v) return dflt;
+  return strtoull(v, nullptr, 10);
+}
 
 template <bool PV, bool PE>
 static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t budget, cudaStream_t s) {
@@ -791,14 +873,19 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
     if ((st = dalloc_t(&light, n + 1, s)) != PB_OK) break;
     if ((st = dalloc_t(&med, n + 1, s)) != PB_OK) break;
     if ((st = dalloc_t(&hkeys, n + 1, s)) != PB_OK) break;
-    k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->wpre, n, p.light_max, p.med_max, light, med, hkeys,
-                                                      g->bitsN, a.acc);
-    count_launch();
+    {
+      PhaseScope ph(PB_PHASE_CLASSIFY, s);
+      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->wpre, n, p.light_max, p.med_max, p.hub_min, light, med,
+                                                        hkeys, g->bitsN, a.acc);
+      count_launch();
+      ph.finish(s);
+    }
     if (cudaMemcpyAsync(hcnt, a.acc, sizeof(hcnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "tier readback: %s", cudaGetErrorString(cudaGetLastError())); break; }
     const uint32_t nl = static_cast<uint32_t>(hcnt[ACC_NLIGHT]), nm = static_cast<uint32_t>(hcnt[ACC_NMED]),
                    nh = static_cast<uint32_t>(hcnt[ACC_NHEAVY]);
     if (nl) {
+      PhaseScope ph(PB_PHASE_LIGHT, s);
       const size_t smem = 2 * LW_WARPS * LW_CAP * sizeof(uint32_t);
       PB_CUDA(cudaFuncSetAttribute(k_light<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
@@ -806,14 +893,17 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
       unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
       unsigned need = (nl + LW_WARPS - 1) / LW_WARPS;
       PB_LAUNCH((k_light<PV, PE>), grid < need ? grid : need, LW_THREADS, smem, s, a, light, nl);
+      ph.finish(s, hcnt[ACC_WLIGHT]);
     }
     if (nm) {
+      PhaseScope ph(PB_PHASE_MEDIUM, s);
       const size_t smem = 2 * MB_CAP * sizeof(uint32_t);
       PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE>, MB_THREADS, smem);
       unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
       PB_LAUNCH((k_medium<PV, PE>), grid < nm ? grid : nm, MB_THREADS, smem, s, a, med, nm);
+      ph.finish(s, hcnt[ACC_WMED]);
     }
     if (nh) {
       if ((st = radix_sort(hkeys, nullptr, nh, 64 - 1, s)) != PB_OK) break;
@@ -822,51 +912,65 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
       count_launch();
       if ((st = dalloc_t(&dmx, 1, s)) != PB_OK) break;
       if (cudaMemsetAsync(dmx, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-      k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, g->wpre, n, dmx);
+      k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, g->wpre, n, g->nU, dmx);
       count_launch();
       unsigned long long hdm = 0;
       if (cudaMemcpyAsync(&hdm, dmx, sizeof(hdm), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "heavy readback"); break; }
       HeavySlots hs = {};
-      hs.n = n;
+      hs.side = g->nU > g->nV ? g->nU : g->nV;
       size_t slot_bytes;
       if (p.dense) {
-        hs.tcap = hdm < n ? hdm : n;
-        slot_bytes = (hs.n + hs.tcap) * sizeof(uint32_t);
+        hs.tcap = hdm < hs.side ? hdm : hs.side;
+        slot_bytes = (hs.side + hs.tcap) * sizeof(uint32_t);
       } else {
         uint64_t cap = 32;
         while (cap < 2 * hdm) cap <<= 1;
         hs.hcap = cap;
         slot_bytes = 2 * cap * sizeof(uint32_t);
       }
-      unsigned cl = p.cluster;
       auto kern = p.dense ? k_heavy<PV, PE, true> : k_heavy<PV, PE, false>;
-      int nc = max_clusters(kern, HB_THREADS, cl);
-      if (nc <= 0) nc = sms / static_cast<int>(cl);
+      // Hubs (wedges > hub_min, the head of the largest-first list) get one
+      // cluster each; the rest one block each (plain batching).
+      const uint32_t nhub = p.cluster > 1 ? static_cast<uint32_t>(hcnt[ACC_NHUB]) : 0;
+      struct Part { const uint32_t *list; uint32_t cnt; unsigned cl; };
+      Part parts[2] = {{heavy, nhub, p.cluster}, {heavy + nhub, nh - nhub, 1}};
       uint64_t fit = budget / (slot_bytes + 16);
       if (fit == 0) { st = fail(PB_ERR_SCRATCH, "scratch budget %llu B below one heavy slot (%llu B)", (unsigned long long)budget, (unsigned long long)slot_bytes); break; }
-      uint64_t nslots = static_cast<uint64_t>(nc);
-      if (nslots > fit) nslots = fit;
-      if (nslots > nh) nslots = nh;
-      size_t need = nslots * slot_bytes + nslots * 3 * sizeof(uint32_t) + 64;
-      if ((st = ensure_scratch(g, need, s)) != PB_OK) break;
-      char *sp = static_cast<char *>(g->scratch);
-      if (p.dense) {
-        hs.A = reinterpret_cast<uint32_t *>(sp);
-        hs.T = hs.A + nslots * hs.n;
-        hs.tcnt = hs.T + nslots * hs.tcap;
-        if (cudaMemsetAsync(hs.A, 0, nslots * hs.n * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-      } else {
-        hs.hkey = reinterpret_cast<uint32_t *>(sp);
-        hs.hval = hs.hkey + nslots * hs.hcap;
-        hs.tcnt = hs.hval + nslots * hs.hcap;
-        if (cudaMemsetAsync(hs.hkey, 0xff, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess ||
-            cudaMemsetAsync(hs.hval, 0, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      PhaseScope ph(PB_PHASE_HEAVY, s);
+      for (const Part &pt : parts) {
+        if (pt.cnt == 0) continue;
+        const unsigned cl = pt.cl;
+        if (cl > 8) PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        int nc = max_clusters(kern, HB_THREADS, cl);
+        if (nc <= 0) nc = sms / static_cast<int>(cl);
+        uint64_t nslots = static_cast<uint64_t>(nc);
+        if (cl > 1 && p.max_slots && nslots > p.max_slots) nslots = p.max_slots;
+        if (nslots > fit) nslots = fit;
+        if (nslots > pt.cnt) nslots = pt.cnt;
+        size_t need = nslots * slot_bytes + nslots * 3 * sizeof(uint32_t) + 64;
+        if ((st = ensure_scratch(g, need, s)) != PB_OK) break;
+        char *sp = static_cast<char *>(g->scratch);
+        if (p.dense) {
+          hs.A = reinterpret_cast<uint32_t *>(sp);
+          hs.T = hs.A + nslots * hs.side;
+          hs.tcnt = hs.T + nslots * hs.tcap;
+          if (cudaMemsetAsync(hs.A, 0, nslots * hs.side * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        } else {
+          hs.hkey = reinterpret_cast<uint32_t *>(sp);
+          hs.hval = hs.hkey + nslots * hs.hcap;
+          hs.tcnt = hs.hval + nslots * hs.hcap;
+          if (cudaMemsetAsync(hs.hkey, 0xff, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess ||
+              cudaMemsetAsync(hs.hval, 0, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        }
+        hs.item = hs.tcnt + 2 * nslots;
+        if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
+            cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, s, a, pt.list, pt.cnt,
+                                 hs)) != PB_OK) break;
       }
-      hs.item = hs.tcnt + 2 * nslots;
-      if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-      if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, s, a,
-                               (const uint32_t *)heavy, nh, hs)) != PB_OK) break;
+      if (st != PB_OK) break;
+      ph.finish(s, hcnt[ACC_WHEAVY]);
     }
   } while (0);
   dfree(light, s); dfree(med, s); dfree(heavy, s); dfree(hkeys, s); dfree(dmx, s);
@@ -955,18 +1059,19 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
   const uint64_t n = g->n, na = 2 * g->m;
   const bool want_pv = o.U || o.V, want_pe = o.E != nullptr;
   uint64_t budget = scratch_bytes ? scratch_bytes : (uint64_t(16) << 30);
-  if (!g->acc) PB_CUDA(cudaMalloc(&g->acc, ACC_WORDS * sizeof(unsigned long long)));
+  if (!g->acc) PB_TRY(dalloc_t(&g->acc, ACC_WORDS, s));
   PB_CUDA(cudaMemsetAsync(g->acc, 0, ACC_WORDS * sizeof(unsigned long long), s));
   if (want_pv) {
-    if (!g->pv) PB_CUDA(cudaMalloc(&g->pv, (n + 1) * sizeof(uint64_t)));
+    if (!g->pv) PB_TRY(dalloc_t(&g->pv, n + 1, s));
     PB_CUDA(cudaMemsetAsync(g->pv, 0, (n + 1) * sizeof(uint64_t), s));
   }
   if (want_pe) {
-    if (!g->es) PB_CUDA(cudaMalloc(&g->es, (na + 1) * sizeof(uint64_t)));
+    if (!g->es) PB_TRY(dalloc_t(&g->es, na + 1, s));
     PB_CUDA(cudaMemsetAsync(g->es, 0, (na + 1) * sizeof(uint64_t), s));
   }
   CArgs a;
   a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.wpre = g->wpre; a.n = n;
+  a.nU = g->nU;
   a.pv = want_pv ? reinterpret_cast<unsigned long long *>(g->pv) : nullptr;
   a.es = want_pe ? reinterpret_cast<unsigned long long *>(g->es) : nullptr;
   a.acc = g->acc;
@@ -978,17 +1083,25 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     p.light_max = LIGHT_MAX;
     p.med_max = MED_MAX;
     p.dense = agg != PB_AGG_HASH;
-    p.cluster = 4;
+    p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", 4));
+    p.max_slots = env_u64("PB_HEAVY_SLOTS", 0);
+    p.hub_min = env_u64("PB_HUB_MIN", uint64_t(1) << 20);
     if (agg == PB_AGG_BATCH) {
       p.med_max = LIGHT_MAX;  // everything above the light tier uses dense arrays
       p.cluster = 1;
+      p.max_slots = 0;
+      p.hub_min = UINT64_MAX;
     }
+    if (p.cluster < 1) p.cluster = 1;
+    if (p.cluster > 16) p.cluster = 16;
     pb_status st;
     if (agg == PB_AGG_SORT) {
+      PhaseScope ph(PB_PHASE_SORT, s);
       if (want_pv && want_pe) st = run_sort<true, true>(g, a, budget, s);
       else if (want_pv) st = run_sort<true, false>(g, a, budget, s);
       else if (want_pe) st = run_sort<false, true>(g, a, budget, s);
       else st = run_sort<false, false>(g, a, budget, s);
+      if (st == PB_OK) ph.finish(s, g->W);
     } else if (want_pv && want_pe) st = run_tiers<true, true>(g, a, p, budget, s);
     else if (want_pv) st = run_tiers<true, false>(g, a, p, budget, s);
     else if (want_pe) st = run_tiers<false, true>(g, a, p, budget, s);
@@ -1007,8 +1120,9 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     if (want_pe) dE = q;
   }
   pb_status st = PB_OK;
+  PhaseScope ph_out(PB_PHASE_OUTPUT, s);
   if (want_pv && n) {
-    k_out_vertex<<<grid_for(n, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->pv), g->rank,
+    k_out_vertex<<<grid_for(n, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->pv), g->label,
                                                          g->nU, g->nV, dU, dV);
     count_launch();
   }
@@ -1026,6 +1140,7 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     if (e != cudaSuccess) st = cuda_fail(e, "output download", __FILE__, __LINE__);
   }
   dfree(tmp, s);
+  if (st == PB_OK) ph_out.finish(s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (st != PB_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "counting kernels", __FILE__, __LINE__);

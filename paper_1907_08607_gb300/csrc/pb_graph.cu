@@ -215,60 +215,83 @@ __global__ void k_custom_rank(const uint32_t *__restrict__ rank_of, uint64_t n, 
 }
 
 // ---------------------------------------------------------------------------
-// Renaming + adjacency in rank space.  Every canonical edge e = (u, v) gives
-// two arcs: 2e from rank(u) to rank(v) and 2e+1 back.  Keys (x << bitsN) |
-// (maxrank - y) sort the arcs by source, then by decreasing neighbour rank.
+// Renaming + adjacency.  Labels: U vertices [0, nU), V vertices [nU, n), each
+// side in rank order.  Every canonical edge e = (u, v) gives two arcs: 2e from
+// u to v and 2e+1 back.  Keys (label(src) << bitsN) | (maxrank - rank(nbr))
+// sort the arcs by source, then by decreasing neighbour rank.
+
+__global__ void k_is_u(const uint32_t *__restrict__ order, uint64_t n, uint32_t nU, uint32_t *__restrict__ f) {
+  for (size_t r = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<size_t>(gridDim.x) * blockDim.x)
+    f[r] = order[r] < nU ? 1u : 0u;
+}
+
+__global__ void k_labels(const uint32_t *__restrict__ order, const uint32_t *__restrict__ cu, uint64_t n,
+                         uint32_t nU, const uint32_t *__restrict__ deg, uint32_t *__restrict__ label,
+                         uint32_t *__restrict__ lrank, uint32_t *__restrict__ degl) {
+  for (size_t r = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t x = order[r];
+    uint32_t l = x < nU ? cu[r] : nU + static_cast<uint32_t>(r - cu[r]);
+    label[x] = l;
+    lrank[l] = static_cast<uint32_t>(r);
+    degl[l] = deg[x];
+  }
+}
 
 __global__ void k_arc_keys(const uint32_t *__restrict__ eu, const uint32_t *__restrict__ ev, uint64_t m,
-                           uint32_t nU, const uint32_t *__restrict__ rank, int bitsN,
-                           uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                           uint32_t nU, const uint32_t *__restrict__ rank, const uint32_t *__restrict__ label,
+                           int bitsN, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   const uint64_t mask = (uint64_t(1) << bitsN) - 1;
   for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
        e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint64_t a = rank[eu[e]], b = rank[nU + ev[e]];
-    keys[2 * e] = (a << bitsN) | (mask - b);
+    uint32_t a = eu[e], b = nU + ev[e];
+    keys[2 * e] = (static_cast<uint64_t>(label[a]) << bitsN) | (mask - rank[b]);
     vals[2 * e] = static_cast<uint32_t>(2 * e);
-    keys[2 * e + 1] = (b << bitsN) | (mask - a);
+    keys[2 * e + 1] = (static_cast<uint64_t>(label[b]) << bitsN) | (mask - rank[a]);
     vals[2 * e + 1] = static_cast<uint32_t>(2 * e + 1);
   }
 }
 
-__global__ void k_rank_degree(const uint32_t *__restrict__ deg, const uint32_t *__restrict__ order,
-                              uint64_t n, uint32_t *__restrict__ degr) {
-  for (size_t r = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
-       r += static_cast<size_t>(gridDim.x) * blockDim.x)
-    degr[r] = deg[order[r]];
-}
-
-__global__ void k_arcs_out(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint64_t na,
-                           int bitsN, uint32_t *__restrict__ adj, uint32_t *__restrict__ slotA,
-                           uint32_t *__restrict__ slotB) {
-  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
+__global__ void k_arcs_out(const uint32_t *__restrict__ vals, uint64_t na, const uint32_t *__restrict__ eu,
+                           const uint32_t *__restrict__ ev, uint32_t nU, const uint32_t *__restrict__ label,
+                           uint32_t *__restrict__ adj, uint32_t *__restrict__ slotA, uint32_t *__restrict__ slotB) {
   for (size_t s = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < na;
        s += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    adj[s] = static_cast<uint32_t>(mask - (keys[s] & mask));
-    uint32_t a = vals[s];
-    if (a & 1u) slotB[a >> 1] = static_cast<uint32_t>(s);
-    else slotA[a >> 1] = static_cast<uint32_t>(s);
+    uint32_t a = vals[s], e = a >> 1;
+    if (a & 1u) {  // arc from v to u
+      adj[s] = label[eu[e]];
+      slotB[e] = static_cast<uint32_t>(s);
+    } else {
+      adj[s] = label[nU + ev[e]];
+      slotA[e] = static_cast<uint32_t>(s);
+    }
   }
 }
 
 // cpos[s] = position of the list owner x in y's list (= deg_x(y), the number
-// of y's neighbours ranked above x, since lists are strictly decreasing);
-// degp[x] = deg_x(x), the length of the prefix of x's list ranked above x.
+// of y's neighbours ranked above x, since lists are strictly decreasing in
+// rank); degp[x] = deg_x(x), the length of the prefix of x's list ranked above
+// x.  Neighbour ranks come from the sort keys, the owner's from lrank.
 __global__ void k_cpos_degp(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                             uint64_t na, int bitsN, const uint32_t *__restrict__ off,
                             const uint32_t *__restrict__ adj, const uint32_t *__restrict__ slotA,
-                            const uint32_t *__restrict__ slotB, uint32_t *__restrict__ cpos,
-                            uint32_t *__restrict__ degp) {
+                            const uint32_t *__restrict__ slotB, const uint32_t *__restrict__ lrank,
+                            uint32_t *__restrict__ cpos, uint32_t *__restrict__ degp) {
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
   for (size_t s = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < na;
        s += static_cast<size_t>(gridDim.x) * blockDim.x) {
     uint32_t a = vals[s];
     uint32_t other = (a & 1u) ? slotA[a >> 1] : slotB[a >> 1];
-    uint32_t y = adj[s];
-    cpos[s] = other - off[y];
+    cpos[s] = other - off[adj[s]];
     uint32_t x = static_cast<uint32_t>(keys[s] >> bitsN);
-    if (y > x && (s + 1 == off[x + 1] || adj[s + 1] < x)) degp[x] = static_cast<uint32_t>(s + 1 - off[x]);
+    uint32_t rx = lrank[x];
+    uint32_t ry = static_cast<uint32_t>(mask - (keys[s] & mask));
+    if (ry > rx) {
+      bool last = s + 1 == off[x + 1];
+      if (!last) last = static_cast<uint32_t>(mask - (keys[s + 1] & mask)) < rx;
+      if (last) degp[x] = static_cast<uint32_t>(s + 1 - off[x]);
+    }
   }
 }
 
@@ -311,37 +334,38 @@ __global__ void k_max_u64(const unsigned long long *__restrict__ a, uint64_t n, 
   if (lane_id() == 0 && mx) atomicMax(out, mx);
 }
 
-void free_ranked(pb_graph *g) {
-  cudaFree(g->rank); cudaFree(g->order); cudaFree(g->off); cudaFree(g->adj); cudaFree(g->cpos);
-  cudaFree(g->degp); cudaFree(g->wpre); cudaFree(g->slotA); cudaFree(g->slotB);
-  g->rank = g->order = g->off = g->adj = g->cpos = g->degp = g->slotA = g->slotB = nullptr;
+void free_ranked(pb_graph *g, cudaStream_t s) {
+  dfree(g->rank, s); dfree(g->order, s); dfree(g->label, s); dfree(g->off, s); dfree(g->adj, s);
+  dfree(g->cpos, s); dfree(g->degp, s); dfree(g->wpre, s); dfree(g->slotA, s); dfree(g->slotB, s);
+  g->rank = g->order = g->label = g->off = g->adj = g->cpos = g->degp = g->slotA = g->slotB = nullptr;
   g->wpre = nullptr;
   g->rank_kind = -1;
   g->W = g->maxw = 0;
 }
 
-static pb_status alloc_ranked(pb_graph *g) {
+static pb_status alloc_ranked(pb_graph *g, cudaStream_t s) {
   const uint64_t n = g->n, na = 2 * g->m;
-  PB_CUDA(cudaMalloc(&g->rank, (n + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->order, (n + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->adj, (na + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->cpos, (na + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->degp, (n + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->wpre, (n + 1) * sizeof(uint64_t)));
-  PB_CUDA(cudaMalloc(&g->slotA, (g->m + 1) * sizeof(uint32_t)));
-  PB_CUDA(cudaMalloc(&g->slotB, (g->m + 1) * sizeof(uint32_t)));
+  PB_TRY(dalloc_t(&g->rank, n + 1, s));
+  PB_TRY(dalloc_t(&g->order, n + 1, s));
+  PB_TRY(dalloc_t(&g->label, n + 1, s));
+  PB_TRY(dalloc_t(&g->off, n + 1, s));
+  PB_TRY(dalloc_t(&g->adj, na + 1, s));
+  PB_TRY(dalloc_t(&g->cpos, na + 1, s));
+  PB_TRY(dalloc_t(&g->degp, n + 1, s));
+  PB_TRY(dalloc_t(&g->wpre, n + 1, s));
+  PB_TRY(dalloc_t(&g->slotA, g->m + 1, s));
+  PB_TRY(dalloc_t(&g->slotB, g->m + 1, s));
   return PB_OK;
 }
 
 pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_device, cudaStream_t s) {
-  free_ranked(g);
+  free_ranked(g, s);
   const uint64_t n = g->n, m = g->m, na = 2 * m;
   const int bitsN = g->bitsN;
-  pb_status st = alloc_ranked(g);
-  if (st != PB_OK) { free_ranked(g); return st; }
+  pb_status st = alloc_ranked(g, s);
+  if (st != PB_OK) { free_ranked(g, s); return st; }
   uint64_t *keys = nullptr;
-  uint32_t *vals = nullptr, *tmp = nullptr, *drank = nullptr;
+  uint32_t *vals = nullptr, *tmp = nullptr, *drank = nullptr, *lrank = nullptr, *cu = nullptr;
   unsigned long long *acc = nullptr, *wc = nullptr;
   unsigned long long hacc[2] = {0, 0};
   do {
@@ -394,10 +418,17 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       dfree(keys, s);
       keys = nullptr;
     }
-    // ---- 2. offsets in rank space
+    // ---- 2. labels (side-major, rank order within a side) and offsets
     if ((st = dalloc_t(&tmp, n + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&cu, n + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&lrank, n + 1, s)) != PB_OK) break;
     if (n) {
-      k_rank_degree<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->deg, g->order, n, tmp);
+      k_is_u<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->order, n, g->nU, tmp);
+      count_launch();
+    }
+    if ((st = scan_u32(tmp, cu, n, s)) != PB_OK) break;
+    if (n) {
+      k_labels<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->order, cu, n, g->nU, g->deg, g->label, lrank, tmp);
       count_launch();
     }
     if ((st = scan_u32(tmp, g->off, n, s)) != PB_OK) break;
@@ -410,13 +441,15 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       // ---- 3. arcs sorted by (source, decreasing neighbour)
       if ((st = dalloc_t(&keys, na, s)) != PB_OK) break;
       if ((st = dalloc_t(&vals, na, s)) != PB_OK) break;
-      k_arc_keys<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, g->rank, bitsN, keys, vals);
+      k_arc_keys<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, g->rank, g->label, bitsN, keys,
+                                                         vals);
       count_launch();
       if ((st = radix_sort(keys, vals, na, 2 * bitsN, s)) != PB_OK) break;
-      k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->adj, g->slotA, g->slotB);
+      k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(vals, na, g->eu, g->ev, g->nU, g->label, g->adj, g->slotA,
+                                                         g->slotB);
       count_launch();
       k_cpos_degp<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->off, g->adj, g->slotA,
-                                                           g->slotB, g->cpos, g->degp);
+                                                           g->slotB, lrank, g->cpos, g->degp);
       count_launch();
       // ---- 4. wedges per first endpoint and the work split prefix
       k_wedges_per_x<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, na, bitsN, g->off, g->degp, g->cpos, wc);
@@ -437,7 +470,8 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
     g->rank_kind = rank_of ? 3 : kind;
   } while (0);
   dfree(keys, s); dfree(vals, s); dfree(tmp, s); dfree(drank, s); dfree(acc, s); dfree(wc, s);
-  if (st != PB_OK) free_ranked(g);
+  dfree(lrank, s); dfree(cu, s);
+  if (st != PB_OK) free_ranked(g, s);
   return st;
 }
 

@@ -113,6 +113,9 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = 16;  // keys per thread
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_BINS = 256;
+static_assert(RS_THREADS == RS_BINS, "one thread per digit in the scatter prefix");
+constexpr int RS_SMEM_KEYS = RS_TILE * 8;
+constexpr int RS_SMEM_VALS = RS_TILE * 12;
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, size_t n,
                                                       int shift, uint32_t *__restrict__ counts,
@@ -131,27 +134,36 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restri
     counts[static_cast<size_t>(d) * ntiles + blockIdx.x] = h[d];
 }
 
+// Scatter of one pass.  Each warp ranks its keys with match_any so that equal
+// digits keep input order; the tile is then staged in shared memory in
+// digit-sorted order and written out in runs, so consecutive threads write
+// consecutive output positions.
 template <bool VALS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, size_t n, int shift, const uint32_t *__restrict__ offs,
     uint32_t ntiles) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t *skey = reinterpret_cast<uint64_t *>(rs_smem);
+  uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+  __shared__ uint32_t tstart[RS_BINS];
+  __shared__ uint32_t gbase[RS_BINS];
+  __shared__ uint32_t s_w[33];
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   // warp w owns keys [base + w*32*IPT, base + (w+1)*32*IPT), round r lane l
   // takes key base + w*32*IPT + r*32 + l: (w, r, l) order is the input order.
-  size_t wbase = static_cast<size_t>(blockIdx.x) * RS_TILE + static_cast<size_t>(w) * 32 * RS_IPT;
+  const size_t tbase = static_cast<size_t>(blockIdx.x) * RS_TILE;
+  const size_t wbase = tbase + static_cast<size_t>(w) * 32 * RS_IPT;
   uint64_t k[RS_IPT];
-  uint32_t v[RS_IPT];
   uint32_t lr[RS_IPT];
 #pragma unroll
   for (int r = 0; r < RS_IPT; r++) {
     size_t i = wbase + static_cast<size_t>(r) * 32 + lane;
     bool valid = i < n;
     k[r] = valid ? kin[i] : 0;
-    if (VALS) v[r] = valid ? vin[i] : 0;
     uint32_t d = valid ? static_cast<uint32_t>((k[r] >> shift) & (RS_BINS - 1)) : 0xffffffffu;
     uint32_t peers = __match_any_sync(FULL, d);
     uint32_t cur = valid ? wcnt[w][d] : 0;
@@ -161,8 +173,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
     lr[r] = cur + __popc(peers & lanemask_lt());
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps
-  for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
+  {
+    // thread d (RS_THREADS == RS_BINS): exclusive prefix over warps, then over digits
+    const int d = threadIdx.x;
     uint32_t run = 0;
 #pragma unroll
     for (int ww = 0; ww < RS_WARPS; ww++) {
@@ -170,6 +183,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
       wcnt[ww][d] = run;
       run += c;
     }
+    uint32_t tot;
+    uint32_t incl = block_incl_scan(run, s_w, &tot);
+    tstart[d] = incl - run;
+    gbase[d] = offs[static_cast<size_t>(d) * ntiles + blockIdx.x] - (incl - run);
   }
   __syncthreads();
 #pragma unroll
@@ -177,11 +194,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
     size_t i = wbase + static_cast<size_t>(r) * 32 + lane;
     if (i < n) {
       uint32_t d = static_cast<uint32_t>((k[r] >> shift) & (RS_BINS - 1));
-      size_t pos = static_cast<size_t>(offs[static_cast<size_t>(d) * ntiles + blockIdx.x]) +
-                   wcnt[w][d] + lr[r];
-      kout[pos] = k[r];
-      if (VALS) vout[pos] = v[r];
+      uint32_t lp = tstart[d] + wcnt[w][d] + lr[r];
+      skey[lp] = k[r];
+      if (VALS) sval[lp] = vin[i];
     }
+  }
+  __syncthreads();
+  const uint32_t nvalid = n - tbase < RS_TILE ? static_cast<uint32_t>(n - tbase) : RS_TILE;
+  for (uint32_t i = threadIdx.x; i < nvalid; i += RS_THREADS) {
+    uint64_t key = skey[i];
+    uint32_t d = static_cast<uint32_t>((key >> shift) & (RS_BINS - 1));
+    size_t pos = static_cast<size_t>(gbase[d]) + i;
+    kout[pos] = key;
+    if (VALS) vout[pos] = sval[i];
   }
 }
 
@@ -196,6 +221,12 @@ pb_status radix_sort(uint64_t *keys, uint32_t *vals, size_t n, int bits, cudaStr
   if (vals) st = dalloc_t(&v2, n, s);
   if (st == PB_OK) st = dalloc_t(&counts, ntiles * RS_BINS, s);
   if (st == PB_OK) st = dalloc_t(&offs, ntiles * RS_BINS + 1, s);
+  static bool attr_set = false;  // per process; the attribute is per function
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_VALS);
+    cudaFuncSetAttribute(k_rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_KEYS);
+    attr_set = true;
+  }
   uint64_t *ka = keys, *kb = k2;
   uint32_t *va = vals, *vb = v2;
   int passes = (bits + 7) / 8;
@@ -207,9 +238,11 @@ pb_status radix_sort(uint64_t *keys, uint32_t *vals, size_t n, int bits, cudaStr
     st = scan_u32(counts, offs, ntiles * RS_BINS, s);
     if (st != PB_OK) break;
     if (vals)
-      k_rs_scatter<true><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, offs, (uint32_t)ntiles);
+      k_rs_scatter<true><<<(unsigned)ntiles, RS_THREADS, RS_SMEM_VALS, s>>>(ka, va, kb, vb, n, shift, offs,
+                                                                           (uint32_t)ntiles);
     else
-      k_rs_scatter<false><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, offs, (uint32_t)ntiles);
+      k_rs_scatter<false><<<(unsigned)ntiles, RS_THREADS, RS_SMEM_KEYS, s>>>(ka, va, kb, vb, n, shift, offs,
+                                                                            (uint32_t)ntiles);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) { st = fail(PB_ERR_CUDA, "radix scatter launch failed"); break; }
     uint64_t *tk = ka; ka = kb; kb = tk;

@@ -161,6 +161,9 @@ def workload(idx: int) -> Graph:
     if idx == 3:
         return chung_lu_graph(seed, 20_000_000, 60_000_000, 300_000_000, 2.0, 2.0,
                               name="cl_20Mx60M_m3e8")
+    if idx == -2:  # quarter-scale copy of workload 2 (profiling)
+        return chung_lu_graph(seed, 250_000, 1_000_000, 12_500_000, 2.1, 2.5,
+                              name="cl_250kx1M_m1.25e7")
     raise KeyError(idx)
 
 
