@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--workload", default="cl2", choices=sorted(WORKLOADS))
     ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree"])
     ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
+    ap.add_argument("--outputs", default="all", choices=["all", "global", "vertex"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -232,7 +233,8 @@ def run_gb300(args):
     def step():
         G = pb.Graph.from_edges(g.nU, g.nV, du, dv)
         G.rank(args.rank)
-        c = G.count_all(args.agg, on_device=True, out=outs)
+        c = G.count_all(args.agg, on_device=True, out=outs, vertex=args.outputs != "global",
+                        edge=args.outputs == "all")
         state["W"] = G.wedges
         state["global"] = c.global_count
         G.free()
@@ -310,7 +312,7 @@ def run_gb300(args):
     roof = None
     if kp["records"] > 0 and kp["ms"] > 0:
         per_launch_ms = kp["ms"] / kp["records"]
-        per_launch_bytes = BYTES_PER_WEDGE["all"] * kp["wedges"] / kp["records"]
+        per_launch_bytes = BYTES_PER_WEDGE[args.outputs] * kp["wedges"] / kp["records"]
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": kern, "peak_source": peak_src,
@@ -326,7 +328,8 @@ def run_gb300(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "rank": args.rank, "agg": args.agg,
-                   "outputs": "global+per-vertex+per-edge", "W": W, "butterflies": state["global"],
+                   "outputs": {"all": "global+per-vertex+per-edge", "global": "global",
+                               "vertex": "global+per-vertex"}[args.outputs], "W": W, "butterflies": state["global"],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (400 MB edge list)"},
         "roofline": roof,
         "cpu_baseline": cpu,

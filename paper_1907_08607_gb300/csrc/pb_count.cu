@@ -134,6 +134,26 @@ __device__ __forceinline__ void warp_locate(uint32_t incl, uint32_t c, uint32_t 
   slot = s_oy + (wi - (s_incl - s_c));
 }
 
+// Adds v into acc[key] for every lane, combining lanes whose keys are equal
+// and adjacent (keys are non-decreasing across the warp, as the flattened
+// wedges of a neighbour chunk are): one shared atomic per run of equal keys
+// instead of one per lane.  All 32 lanes must call it; inactive lanes pass
+// v = 0.
+__device__ __forceinline__ void warp_run_add(unsigned long long *acc, uint32_t key, unsigned long long v) {
+  const uint32_t lane = lane_id();
+  const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const uint32_t heads = __ballot_sync(FULL, head);
+  // segmented inclusive scan from the right: each run head gets its run's sum
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long u = __shfl_down_sync(FULL, v, o);
+    // lane + o is in this lane's run iff no run head lies in (lane, lane + o]
+    if (lane + o < 32 && (heads & (((1u << o) - 1u) << (lane + 1))) == 0) v += u;
+  }
+  if (head && v) atomicAdd(&acc[key], v);
+}
+
 // ---------------------------------------------------------------------------
 // Light tier: one warp per first endpoint.
 template <bool PV, bool PE>
@@ -190,14 +210,15 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
           const uint32_t wi = wb + lane;
           uint32_t src, slot;
           warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
+          unsigned long long t = 0;
           if (wi < tot) {
             uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
             if (d > 1) {
-              unsigned long long t = d - 1;
+              t = d - 1;
               if (PE) atomicAdd(&a.es[slot], t);
-              atomicAdd(&s_sum[w][src], t);
             }
           }
+          warp_run_add(s_sum[w], src, t);
         }
         __syncwarp();
         if (v) {
@@ -295,15 +316,20 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
         s_ex[tid] = incl - c;
         s_oy[tid] = v ? a.off[y] : 0;
         __syncthreads();
-        for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
-          uint32_t src = block_find(s_incl, MB_THREADS, wi);
-          uint32_t slot = s_oy[src] + (wi - s_ex[src]);
-          uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
-          if (d > 1) {
-            unsigned long long t = d - 1;
-            if (PE) atomicAdd(&a.es[slot], t);
-            atomicAdd(&s_sum[src], t);
+        for (uint32_t wb = 0; wb < tot; wb += MB_THREADS) {
+          const uint32_t wi = wb + tid;
+          uint32_t src = 0;
+          unsigned long long t = 0;
+          if (wi < tot) {
+            src = block_find(s_incl, MB_THREADS, wi);
+            uint32_t slot = s_oy[src] + (wi - s_ex[src]);
+            uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
+            if (d > 1) {
+              t = d - 1;
+              if (PE) atomicAdd(&a.es[slot], t);
+            }
           }
+          warp_run_add(s_sum, src, t);
         }
         __syncthreads();
         if (v) {
@@ -542,11 +568,9 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
             dv[q] = wb + q * HB_THREADS + tid < hi ? heavy_get<DENSE>(h, slot, A, lg, x2v[q], base, err) : 0;
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++) {
-            if (dv[q] > 1) {
-              unsigned long long t = dv[q] - 1;
-              if (PE) atomicAdd(&a.es[slv[q]], t);
-              atomicAdd(&s_sum[srcv[q]], t);
-            }
+            unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
+            if (PE && t) atomicAdd(&a.es[slv[q]], t);
+            warp_run_add(s_sum, srcv[q], t);
           }
         }
         __syncthreads();
@@ -629,22 +653,27 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
       s_ex[tid] = incl - c;
       s_oy[tid] = v ? a.off[y] : 0;
       __syncthreads();
-      for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
-        uint32_t src = block_find(s_incl, MB_THREADS, wi);
-        uint32_t slot = s_oy[src] + (wi - s_ex[src]);
-        uint32_t x2 = a.adj[slot];
-        if (EMIT) {
-          out[done + wi] = kx | x2;
-        } else {
-          uint32_t r = lower_bound_u64(ukey, s0, s1, kx | x2);
-          uint32_t d = (r < s1 && ukey[r] == (kx | x2)) ? ud[r] : 0;
-          if (d == 0) atomicOr(&a.acc[ACC_ERR], 32ull);
-          if (d > 1) {
-            unsigned long long t = d - 1;
-            if (PE) atomicAdd(&a.es[slot], t);
-            atomicAdd(&s_sum[src], t);
+      for (uint32_t wb = 0; wb < tot; wb += MB_THREADS) {
+        const uint32_t wi = wb + tid;
+        uint32_t src = 0;
+        unsigned long long t = 0;
+        if (wi < tot) {
+          src = block_find(s_incl, MB_THREADS, wi);
+          uint32_t slot = s_oy[src] + (wi - s_ex[src]);
+          uint32_t x2 = a.adj[slot];
+          if (EMIT) {
+            out[done + wi] = kx | x2;
+          } else {
+            uint32_t r = lower_bound_u64(ukey, s0, s1, kx | x2);
+            uint32_t d = (r < s1 && ukey[r] == (kx | x2)) ? ud[r] : 0;
+            if (d == 0) atomicOr(&a.acc[ACC_ERR], 32ull);
+            if (d > 1) {
+              t = d - 1;
+              if (PE) atomicAdd(&a.es[slot], t);
+            }
           }
         }
+        if (!EMIT) warp_run_add(s_sum, src, t);
       }
       __syncthreads();
       if (!EMIT && v) {
@@ -1083,9 +1112,9 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     p.light_max = LIGHT_MAX;
     p.med_max = MED_MAX;
     p.dense = agg != PB_AGG_HASH;
-    p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", 4));
+    p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", 2));
     p.max_slots = env_u64("PB_HEAVY_SLOTS", 0);
-    p.hub_min = env_u64("PB_HUB_MIN", uint64_t(1) << 20);
+    p.hub_min = env_u64("PB_HUB_MIN", uint64_t(1) << 18);
     if (agg == PB_AGG_BATCH) {
       p.med_max = LIGHT_MAX;  // everything above the light tier uses dense arrays
       p.cluster = 1;
