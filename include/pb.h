@@ -159,6 +159,37 @@ pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info);
 /* Releases the graph and every device buffer it holds.  NULL is accepted. */
 pb_status pb_graph_free(pb_graph *g);
 
+/* Counting without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory -- a host runtime that owns all device memory through its own
+ * pool and forbids driver allocations after start-up, or a latency-critical
+ * loop that must not risk the implicit synchronisation of cudaMalloc/cudaFree.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Input: an already preprocessed graph in device memory, caller-owned, in the
+ * layout PREPROCESS produces: n vertices labelled so that U is [0, nU) and V
+ * is [nU, n), each side in increasing rank order; off[n + 1] (uint32) CSR
+ * offsets by label; adj[off[n]] neighbour labels, each list in decreasing
+ * rank order; cpos[off[n]], for the entry holding y in x's list, the position
+ * of x in y's list (the number of y's neighbours ranked above x); degp[n], the
+ * number of x's neighbours ranked above x.
+ * Output (device, caller-owned): *out_global, and out_pv[n] per label when
+ * out_pv is not NULL (butterflies per vertex).  Both are cleared by the call.
+ *
+ * Scratch: a file-scope device array of 128 MiB in the library, held by every
+ * GPU that loads the library until the process exits.  A side (nU or n - nU)
+ * of more than 16,777,184 vertices does not fit and is rejected with
+ * PB_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array and leaves its
+ * contents behind; the call clears what must start at zero.  Calls whose
+ * device work overlaps (other streams, other threads) race on the array and
+ * must be serialised by the caller.  Returns after the stream has completed
+ * the work; PB_ERR_OVERFLOW if the global count exceeds 2^64. */
+pb_status pb_count_noalloc(uint64_t n, uint32_t nU, const uint32_t *off, const uint32_t *adj,
+                           const uint32_t *cpos, const uint32_t *degp, uint64_t *out_global,
+                           uint64_t *out_pv, void *stream);
+
 /* Number of device kernels the library has launched in this process (all
  * graphs, all devices); used to report launch counts. */
 uint64_t pb_kernel_launches(void);

@@ -33,7 +33,7 @@ STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 
 ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ranks", "pb_count_global",
                "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
                "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string",
-               "pb_profile_enable", "pb_profile_reset", "pb_profile_read"]
+               "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc"]
 
 PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH):
         lib.pb_profile_reset.restype = None
         lib.pb_profile_read.argtypes = [ctypes.POINTER(Profile)]
         lib.pb_profile_read.restype = i32
+        lib.pb_count_noalloc.argtypes = [u64, u32, vp, vp, vp, vp, vp, vp, vp]
+        lib.pb_count_noalloc.restype = i32
         _lib = lib
         return lib
 
@@ -151,6 +153,21 @@ def _edge_arg(x, torch):
         return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
     a = np.ascontiguousarray(x, dtype=np.uint32)
     return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+def count_noalloc(n: int, nU: int, off, adj, cpos, degp, out_global, out_pv=None, stream=None) -> None:
+    """pb_count_noalloc: counts on an already preprocessed graph held in
+    caller-owned device tensors, with no device allocation by the library (for
+    callers whose runtime owns all device memory).  Inputs are int32/uint32
+    CUDA tensors in the layout of include/pb.h; out_global is a 1-element and
+    out_pv an n-element int64 CUDA tensor (uint64 bit patterns)."""
+    lib = load_library()
+    for t in (off, adj, cpos, degp, out_global) + ((out_pv,) if out_pv is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("pb_count_noalloc takes contiguous CUDA tensors")
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    _check(lib.pb_count_noalloc(n, nU, p(off), p(adj), p(cpos), p(degp), p(out_global), p(out_pv),
+                                _stream(stream)))
 
 
 @dataclass
