@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree"])
     ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
     ap.add_argument("--outputs", default="all", choices=["all", "global", "vertex"])
+    ap.add_argument("--retrieval", default="auto", choices=["low", "high", "auto"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -233,6 +234,7 @@ def run_gb300(args):
     def step():
         G = pb.Graph.from_edges(g.nU, g.nV, du, dv)
         G.rank(args.rank)
+        G.set_retrieval(args.retrieval)
         c = G.count_all(args.agg, on_device=True, out=outs, vertex=args.outputs != "global",
                         edge=args.outputs == "all")
         state["W"] = G.wedges
@@ -283,6 +285,7 @@ def run_gb300(args):
         def step_host():
             G = pb.Graph.from_edges(g.nU, g.nV, hu, hv)
             G.rank(args.rank)
+            G.set_retrieval(args.retrieval)
             G.count_all(args.agg, on_device=False, out=hout)
             G.free()
 
@@ -328,6 +331,7 @@ def run_gb300(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "rank": args.rank, "agg": args.agg,
+                   "retrieval": args.retrieval,
                    "outputs": {"all": "global+per-vertex+per-edge", "global": "global",
                                "vertex": "global+per-vertex"}[args.outputs], "W": W, "butterflies": state["global"],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (400 MB edge list)"},

@@ -77,6 +77,22 @@ typedef enum {
   PB_AGG_AUTO = 4
 } pb_agg;
 
+/* Which endpoint of a wedge owns it during aggregation.
+ *  LOW:  the lower-ranked endpoint x1 (Algorithm 2): x1 walks its neighbours y
+ *        ranked above it and, for each, the entries of y's list ranked above
+ *        x1, and groups them by the second endpoint.
+ *  HIGH: the higher-ranked endpoint (the cache optimisation of Wang et al.
+ *        described in Sec. "Other options"): the same wedges, each grouped at
+ *        its higher-ranked endpoint by the lower one.  Owners then have far
+ *        fewer wedges each, and the grouping keys concentrate on the few
+ *        lowest-ranked (highest-degree) vertices.
+ *  AUTO: HIGH.  Counts and the wedge total W are the same either way. */
+typedef enum {
+  PB_RETRIEVE_LOW = 0,
+  PB_RETRIEVE_HIGH = 1,
+  PB_RETRIEVE_AUTO = 2
+} pb_retrieval;
+
 typedef enum {
   PB_OK = 0,
   PB_ERR_INVALID = 1,  /* bad argument, id out of range, size over a limit */
@@ -95,7 +111,7 @@ typedef struct {
   uint32_t max_deg_U, max_deg_V;
   int32_t rank_kind;   /* pb_rank_kind, 3 = custom ranking, -1 = not ranked */
   uint64_t W;          /* wedges retrieved under the current ranking */
-  uint64_t max_wedges_x1; /* largest wedge count of a single first endpoint */
+  uint64_t max_wedges_x1; /* largest wedge count of one lower-ranked endpoint */
   uint64_t device_bytes;  /* device memory held by the graph (scratch included) */
 } pb_graph_info_t;
 
@@ -122,6 +138,9 @@ pb_status pb_rank(pb_graph *g, pb_rank_kind kind, void *stream);
  * selects).  PB_ERR_INVALID if it is not a permutation.  Counts do not depend
  * on the ranking (Sec. "Preprocessing"); only the retrieved wedges do. */
 pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, void *stream);
+
+/* Selects the wedge owner used by later counts on g (default AUTO). */
+pb_status pb_set_retrieval(pb_graph *g, pb_retrieval r);
 
 /* Writes rank_of[x] for every global id x (host or device). */
 pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream);

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpb.so")
 
 RANKS = {"side": 0, "degree": 1, "approx_degree": 2}
 AGGS = {"sort": 0, "hash": 1, "hist": 2, "batch": 3, "auto": 4}
+RETRIEVALS = {"low": 0, "high": 1, "auto": 2}
 STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 4: "PB_ERR_SCRATCH",
           5: "PB_ERR_TIMEOUT", 6: "PB_ERR_OVERFLOW"}
 
@@ -33,7 +34,8 @@ STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 
 ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ranks", "pb_count_global",
                "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
                "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string",
-               "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc"]
+               "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc",
+               "pb_set_retrieval"]
 
 PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
@@ -103,6 +105,8 @@ def load_library(path: str = LIB_PATH):
         lib.pb_profile_read.restype = i32
         lib.pb_count_noalloc.argtypes = [u64, u32, vp, vp, vp, vp, vp, vp, vp]
         lib.pb_count_noalloc.restype = i32
+        lib.pb_set_retrieval.argtypes = [vp, i32]
+        lib.pb_set_retrieval.restype = i32
         _lib = lib
         return lib
 
@@ -227,6 +231,12 @@ class Graph:
         torch = _torch()
         p, dev, keep = _edge_arg(rank_of, torch)
         _check(load_library().pb_rank_custom(self._h, p, dev, _stream(stream)))
+        return self
+
+    def set_retrieval(self, which: str = "auto") -> "Graph":
+        """Wedge owner for later counts: "low" (Algorithm 2), "high" (the
+        cache optimisation) or "auto"."""
+        _check(load_library().pb_set_retrieval(self._h, RETRIEVALS[which]))
         return self
 
     def ranks(self, stream=None) -> np.ndarray:

@@ -290,6 +290,14 @@ pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, vo
   return PB_OK;
 }
 
+pb_status pb_set_retrieval(pb_graph *g, pb_retrieval r) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  if (r < PB_RETRIEVE_LOW || r > PB_RETRIEVE_AUTO) return fail(PB_ERR_INVALID, "unknown retrieval %d", (int)r);
+  g->retrieval = r;
+  return PB_OK;
+}
+
 pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream) {
   clear_error();
   if (!g || !rank_of) return fail(PB_ERR_INVALID, "graph or rank_of is NULL");

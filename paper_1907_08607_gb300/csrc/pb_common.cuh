@@ -40,11 +40,14 @@ struct pb_graph {
   uint32_t *adj = nullptr;    // [2m] neighbour labels, decreasing rank within a list
   uint32_t *cpos = nullptr;   // [2m] for slot (x, y): position of x in y's list = deg_x(y)
   uint32_t *degp = nullptr;   // [n] deg_x(x): neighbours ranked above x
-  uint64_t *wpre = nullptr;   // [n + 1] exclusive prefix of wedges per first endpoint
+  uint64_t *wpre = nullptr;   // [n + 1] exclusive prefix of wedges per lower-ranked endpoint
+  uint64_t *wpre_rev = nullptr;  // [n + 1] the same per higher-ranked endpoint
   uint32_t *slotA = nullptr;  // [m] slot of canonical edge e in its U endpoint's list
   uint32_t *slotB = nullptr;  // [m] slot of e in its V endpoint's list
   uint64_t W = 0;
-  uint64_t maxw = 0;          // max wedges of one first endpoint
+  uint64_t maxw = 0;          // max wedges of one lower-ranked endpoint
+  uint64_t maxw_rev = 0;      // max wedges of one higher-ranked endpoint
+  int retrieval = PB_RETRIEVE_AUTO;
 
   // Aggregation scratch, grown on demand and kept until pb_graph_free.
   void *scratch = nullptr;

@@ -42,6 +42,7 @@ struct CArgs {
   const uint64_t *__restrict__ wpre;
   uint64_t n;
   uint32_t nU;              // labels [0, nU) are U vertices, [nU, n) V vertices
+  int rev;                  // 1: wedges are owned by their higher-ranked endpoint
   unsigned long long *pv;   // [n] by label, or null
   unsigned long long *es;   // [2m] per slot, or null
   unsigned long long *acc;  // [0] global, [1] overflow, [2..] work queues
@@ -102,16 +103,51 @@ __device__ __forceinline__ uint32_t sh_get(const uint32_t *key, const uint32_t *
   return cnt[h];
 }
 
-// Bound on the distinct second endpoints of x1: its wedges, and the vertices
-// of its own side ranked above it (labels above x1 up to the side's end).
-__device__ __forceinline__ uint64_t distinct_bound(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1) {
-  uint64_t side_end = x1 < nU ? nU : n;
-  uint64_t above = side_end - 1 - x1;
-  return wc < above ? wc : above;
+// Bound on the distinct other endpoints of an owner x: its wedges, and the
+// vertices of its own side on the far side of it in rank order (labels above x
+// up to the side's end when x owns as the lower endpoint, labels below x down
+// to the side's start when it owns as the higher one).
+__device__ __forceinline__ uint64_t distinct_bound(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x, int rev) {
+  uint64_t side_end = x < nU ? nU : n, side_begin = x < nU ? 0 : nU;
+  uint64_t room = rev ? x - side_begin : side_end - 1 - x;
+  return wc < room ? wc : room;
 }
 
-__device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1) {
-  uint64_t dmax = distinct_bound(wc, n, nU, x1);
+// Neighbour i of owner x (slot xbase + i): its label y, the number c of
+// wedges through y that x owns, and the slot oy in y's list where their other
+// endpoints start.  Owning as the lower endpoint (Algorithm 2): the first
+// deg_x(y) entries of y's list.  Owning as the higher endpoint (the cache
+// optimisation of Sec. "Other options"): the entries of y's list ranked below
+// both y and x, a suffix starting after deg_y(y) and after x's own position.
+__device__ __forceinline__ void owner_nbr(const CArgs &a, uint32_t xbase, uint32_t i, bool v, uint32_t &y,
+                                          uint32_t &c, uint32_t &oy) {
+  if (!v) {
+    y = 0; c = 0; oy = 0;
+    return;
+  }
+  const uint32_t sl = xbase + i;
+  y = a.adj[sl];
+  const uint32_t p = a.cpos[sl];
+  const uint32_t o0 = a.off[y];
+  if (!a.rev) {
+    c = p;
+    oy = o0;
+    return;
+  }
+  const uint32_t dy = a.off[y + 1] - o0;
+  uint32_t st = a.degp[y];
+  if (p + 1 > st) st = p + 1;
+  c = dy > st ? dy - st : 0;
+  oy = o0 + st;
+}
+
+// Number of neighbours of owner x that can carry its wedges.
+__device__ __forceinline__ uint32_t owner_span(const CArgs &a, uint32_t x) {
+  return a.rev ? a.off[x + 1] - a.off[x] : a.degp[x];
+}
+
+__device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1, int rev) {
+  uint64_t dmax = distinct_bound(wc, n, nU, x1, rev);
   int lg = 5;
   while ((uint64_t(1) << lg) < 2 * dmax) lg++;
   return lg;
@@ -168,15 +204,16 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
   for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
     const uint32_t x1 = list[it];
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = table_lg(wc, a.n, a.nU, x1);
+    const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
     for (uint32_t t = lane; t < cap; t += 32) { key[t] = EMPTY; cnt[t] = 0; }
     __syncwarp();
-    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
       const uint32_t i = k0 + lane;
       const bool v = i < dp;
-      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0, oy = v ? a.off[y] : 0;
+      uint32_t y, c, oy;
+      owner_nbr(a, base, i, v, y, c, oy);
       const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
       for (uint32_t wb = 0; wb < tot; wb += 32) {
         const uint32_t wi = wb + lane;
@@ -204,7 +241,8 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
       for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
         const uint32_t i = k0 + lane;
         const bool v = i < dp;
-        const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0, oy = v ? a.off[y] : 0;
+        uint32_t y, c, oy;
+        owner_nbr(a, base, i, v, y, c, oy);
         const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
         for (uint32_t wb = 0; wb < tot; wb += 32) {
           const uint32_t wi = wb + lane;
@@ -270,20 +308,21 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
     if (it >= nlist) break;
     const uint32_t x1 = list[it];
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = table_lg(wc, a.n, a.nU, x1);
+    const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
     for (uint32_t t = tid; t < cap; t += MB_THREADS) { key[t] = EMPTY; cnt[t] = 0; }
     __syncthreads();
-    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
       const uint32_t i = k0 + tid;
       const bool v = i < dp;
-      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+      uint32_t y, c, oy;
+      owner_nbr(a, base, i, v, y, c, oy);
       uint32_t tot;
       const uint32_t incl = block_incl_scan(c, s_w, &tot);
       s_incl[tid] = incl;
       s_ex[tid] = incl - c;
-      s_oy[tid] = v ? a.off[y] : 0;
+      s_oy[tid] = oy;
       __syncthreads();
       for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
         uint32_t src = block_find(s_incl, MB_THREADS, wi);
@@ -309,12 +348,13 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
       for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
         const uint32_t i = k0 + tid;
         const bool v = i < dp;
-        const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+        uint32_t y, c, oy;
+        owner_nbr(a, base, i, v, y, c, oy);
         uint32_t tot;
         const uint32_t incl = block_incl_scan(c, s_w, &tot);
         s_incl[tid] = incl;
         s_ex[tid] = incl - c;
-        s_oy[tid] = v ? a.off[y] : 0;
+        s_oy[tid] = oy;
         __syncthreads();
         for (uint32_t wb = 0; wb < tot; wb += MB_THREADS) {
           const uint32_t wi = wb + tid;
@@ -462,18 +502,19 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
     const uint32_t x1 = list[it];
     const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = DENSE ? 0 : table_lg(wc, a.n, a.nU, x1);
-    const uint32_t xbase = a.off[x1], dp = a.degp[x1];
+    const int lg = DENSE ? 0 : table_lg(wc, a.n, a.nU, x1, a.rev);
+    const uint32_t xbase = a.off[x1], dp = owner_span(a, x1);
     // ---- aggregate
     for (uint32_t k0 = 0; k0 < dp; k0 += HB_THREADS) {
       const uint32_t i = k0 + tid;
       const bool v = i < dp;
-      const uint32_t y = v ? a.adj[xbase + i] : 0, c = v ? a.cpos[xbase + i] : 0;
+      uint32_t y, c, oy;
+      owner_nbr(a, xbase, i, v, y, c, oy);
       uint32_t tot;
       const uint32_t incl = block_incl_scan(c, s_w, &tot);
       s_incl[tid] = incl;
       s_ex[tid] = incl - c;
-      s_oy[tid] = v ? a.off[y] : 0;
+      s_oy[tid] = oy;
       __syncthreads();
       const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(tot) * crank / csize);
       const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(tot) * (crank + 1) / csize);
@@ -540,12 +581,13 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
       for (uint32_t k0 = 0; k0 < dp; k0 += HB_THREADS) {
         const uint32_t i = k0 + tid;
         const bool v = i < dp;
-        const uint32_t y = v ? a.adj[xbase + i] : 0, c = v ? a.cpos[xbase + i] : 0;
+        uint32_t y, c, oy;
+        owner_nbr(a, xbase, i, v, y, c, oy);
         uint32_t tot;
         const uint32_t incl = block_incl_scan(c, s_w, &tot);
         s_incl[tid] = incl;
         s_ex[tid] = incl - c;
-        s_oy[tid] = v ? a.off[y] : 0;
+        s_oy[tid] = oy;
         __syncthreads();
         const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(tot) * crank / csize);
         const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(tot) * (crank + 1) / csize);
@@ -638,7 +680,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
     const uint32_t x1 = s_item;
     if (x1 >= hi) break;
     const uint64_t kx = static_cast<uint64_t>(x1 - lo) << bitsN;
-    const uint32_t base = a.off[x1], dp = a.degp[x1];
+    const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     uint64_t *out = EMIT ? keys + (a.wpre[x1] - wbase) : nullptr;
     uint32_t s0 = 0, s1 = 0;
     if (!EMIT) { s0 = seg[x1 - lo]; s1 = seg[x1 - lo + 1]; }
@@ -646,12 +688,13 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
     for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
       const uint32_t i = k0 + tid;
       const bool v = i < dp;
-      const uint32_t y = v ? a.adj[base + i] : 0, c = v ? a.cpos[base + i] : 0;
+      uint32_t y, c, oy;
+      owner_nbr(a, base, i, v, y, c, oy);
       uint32_t tot;
       const uint32_t incl = block_incl_scan(c, s_w, &tot);
       s_incl[tid] = incl;
       s_ex[tid] = incl - c;
-      s_oy[tid] = v ? a.off[y] : 0;
+      s_oy[tid] = oy;
       __syncthreads();
       for (uint32_t wb = 0; wb < tot; wb += MB_THREADS) {
         const uint32_t wi = wb + tid;
@@ -788,11 +831,11 @@ __global__ void k_keys_low(const uint64_t *__restrict__ keys, uint32_t nk, int b
 }
 
 __global__ void k_max_wedges_list(const uint32_t *__restrict__ list, uint32_t nl, const uint64_t *__restrict__ wpre,
-                                  uint64_t n, uint32_t nU, unsigned long long *out) {
+                                  uint64_t n, uint32_t nU, int rev, unsigned long long *out) {
   unsigned long long mx = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
     uint32_t x = list[i];
-    unsigned long long dm = distinct_bound(wpre[x + 1] - wpre[x], n, nU, x);
+    unsigned long long dm = distinct_bound(wpre[x + 1] - wpre[x], n, nU, x, rev);
     mx = dm > mx ? dm : mx;
   }
 #pragma unroll
@@ -904,7 +947,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
     if ((st = dalloc_t(&hkeys, n + 1, s)) != PB_OK) break;
     {
       PhaseScope ph(PB_PHASE_CLASSIFY, s);
-      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->wpre, n, p.light_max, p.med_max, p.hub_min, light, med,
+      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, p.light_max, p.med_max, p.hub_min, light, med,
                                                         hkeys, g->bitsN, a.acc);
       count_launch();
       ph.finish(s);
@@ -941,7 +984,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
       count_launch();
       if ((st = dalloc_t(&dmx, 1, s)) != PB_OK) break;
       if (cudaMemsetAsync(dmx, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-      k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, g->wpre, n, g->nU, dmx);
+      k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, a.wpre, n, g->nU, a.rev, dmx);
       count_launch();
       unsigned long long hdm = 0;
       if (cudaMemcpyAsync(&hdm, dmx, sizeof(hdm), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1014,8 +1057,9 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, cudaStre
   const uint64_t per_wedge = 8 + 8 + 4 + 4 + 8 + 4 + 4;
   uint64_t cap = budget / per_wedge;
   if (cap > (uint64_t(1) << 31)) cap = uint64_t(1) << 31;
-  if (cap < g->maxw) return fail(PB_ERR_SCRATCH, "sort aggregation: one first endpoint has %llu wedges, budget holds %llu",
-                                 (unsigned long long)g->maxw, (unsigned long long)cap);
+  const uint64_t maxw = a.rev ? g->maxw_rev : g->maxw;
+  if (cap < maxw) return fail(PB_ERR_SCRATCH, "sort aggregation: one owner has %llu wedges, budget holds %llu",
+                              (unsigned long long)maxw, (unsigned long long)cap);
   unsigned long long *dchunk = nullptr;
   uint64_t *keys = nullptr, *ukey = nullptr;
   uint32_t *head = nullptr, *cid = nullptr, *rstart = nullptr, *ud = nullptr, *seg = nullptr;
@@ -1033,7 +1077,7 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, cudaStre
     const int sms = sm_count(g->device);
     uint32_t lo = 0;
     while (lo < n && st == PB_OK) {
-      k_chunk_end<<<1, 1, 0, s>>>(g->wpre, n, lo, cap, dchunk);
+      k_chunk_end<<<1, 1, 0, s>>>(a.wpre, n, lo, cap, dchunk);
       count_launch();
       unsigned long long hc[2];
       if (cudaMemcpyAsync(hc, dchunk, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1042,7 +1086,7 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, cudaStre
       const uint64_t cnt = hc[1];
       if (cnt > 0) {
         uint64_t wbase = 0;
-        if (cudaMemcpyAsync(&wbase, g->wpre + lo, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
+        if (cudaMemcpyAsync(&wbase, a.wpre + lo, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
         cudaStreamSynchronize(s);
         if (cudaMemsetAsync(a.acc + ACC_QMED, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         unsigned grid = static_cast<unsigned>(sms * 4);
@@ -1099,7 +1143,11 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     PB_CUDA(cudaMemsetAsync(g->es, 0, (na + 1) * sizeof(uint64_t), s));
   }
   CArgs a;
-  a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.wpre = g->wpre; a.n = n;
+  // Owner of each wedge: its lower-ranked endpoint (Algorithm 2) or, with the
+  // cache optimisation, its higher-ranked one.  Same wedges either way.
+  a.rev = g->retrieval == PB_RETRIEVE_LOW ? 0 : 1;
+  a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.n = n;
+  a.wpre = a.rev ? g->wpre_rev : g->wpre;
   a.nU = g->nU;
   a.pv = want_pv ? reinterpret_cast<unsigned long long *>(g->pv) : nullptr;
   a.es = want_pe ? reinterpret_cast<unsigned long long *>(g->es) : nullptr;

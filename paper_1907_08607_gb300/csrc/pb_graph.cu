@@ -321,6 +321,33 @@ __global__ void k_wedges_per_x(const uint64_t *__restrict__ keys, uint64_t na, i
   }
 }
 
+// Wedges owned by their higher-ranked endpoint x: for each neighbour y (slot
+// s of x), the entries of y's list ranked below both y and x.
+__global__ void k_wedges_rev(const uint64_t *__restrict__ keys, uint64_t na, int bitsN,
+                             const uint32_t *__restrict__ off, const uint32_t *__restrict__ degp,
+                             const uint32_t *__restrict__ adj, const uint32_t *__restrict__ cpos,
+                             unsigned long long *__restrict__ wc) {
+  size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  size_t iters = (na + stride - 1) / stride;
+  for (size_t it = 0; it < iters; it++) {
+    size_t s = start + it * stride;
+    bool valid = s < na;
+    uint32_t x = valid ? static_cast<uint32_t>(keys[s] >> bitsN) : 0xffffffffu;
+    unsigned long long c = 0;
+    if (valid) {
+      uint32_t y = adj[s], p = cpos[s], dy = off[y + 1] - off[y], st = degp[y];
+      if (p + 1 > st) st = p + 1;
+      c = dy > st ? dy - st : 0;
+    }
+    uint32_t peers = __match_any_sync(FULL, x);
+    uint32_t leader = __ffs(peers) - 1;
+    unsigned long long tot = 0;
+    for (uint32_t q = peers; q; q &= q - 1) tot += __shfl_sync(peers, c, __ffs(q) - 1);
+    if (valid && lane_id() == leader && tot) atomicAdd(&wc[x], tot);
+  }
+}
+
 __global__ void k_max_u64(const unsigned long long *__restrict__ a, uint64_t n, unsigned long long *out) {
   unsigned long long mx = 0;
   for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
@@ -336,11 +363,12 @@ __global__ void k_max_u64(const unsigned long long *__restrict__ a, uint64_t n, 
 
 void free_ranked(pb_graph *g, cudaStream_t s) {
   dfree(g->rank, s); dfree(g->order, s); dfree(g->label, s); dfree(g->off, s); dfree(g->adj, s);
-  dfree(g->cpos, s); dfree(g->degp, s); dfree(g->wpre, s); dfree(g->slotA, s); dfree(g->slotB, s);
+  dfree(g->cpos, s); dfree(g->degp, s); dfree(g->wpre, s); dfree(g->wpre_rev, s); dfree(g->slotA, s);
+  dfree(g->slotB, s);
   g->rank = g->order = g->label = g->off = g->adj = g->cpos = g->degp = g->slotA = g->slotB = nullptr;
-  g->wpre = nullptr;
+  g->wpre = g->wpre_rev = nullptr;
   g->rank_kind = -1;
-  g->W = g->maxw = 0;
+  g->W = g->maxw = g->maxw_rev = 0;
 }
 
 static pb_status alloc_ranked(pb_graph *g, cudaStream_t s) {
@@ -353,6 +381,7 @@ static pb_status alloc_ranked(pb_graph *g, cudaStream_t s) {
   PB_TRY(dalloc_t(&g->cpos, na + 1, s));
   PB_TRY(dalloc_t(&g->degp, n + 1, s));
   PB_TRY(dalloc_t(&g->wpre, n + 1, s));
+  PB_TRY(dalloc_t(&g->wpre_rev, n + 1, s));
   PB_TRY(dalloc_t(&g->slotA, g->m + 1, s));
   PB_TRY(dalloc_t(&g->slotB, g->m + 1, s));
   return PB_OK;
@@ -456,17 +485,31 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       count_launch();
     }
     if ((st = scan_u64(reinterpret_cast<uint64_t *>(wc), g->wpre, n, s)) != PB_OK) break;
-    if (cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if (cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
     if (n) {
       k_max_u64<<<grid_for(n, 256, 2048), 256, 0, s>>>(wc, n, acc);
       count_launch();
     }
-    uint64_t hW = 0;
+    // the same wedges counted at their higher-ranked endpoint
+    if (cudaMemsetAsync(wc, 0, (n + 1) * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if (na > 0) {
+      k_wedges_rev<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, na, bitsN, g->off, g->degp, g->adj, g->cpos, wc);
+      count_launch();
+    }
+    if ((st = scan_u64(reinterpret_cast<uint64_t *>(wc), g->wpre_rev, n, s)) != PB_OK) break;
+    if (n) {
+      k_max_u64<<<grid_for(n, 256, 2048), 256, 0, s>>>(wc, n, acc + 1);
+      count_launch();
+    }
+    uint64_t hW = 0, hWr = 0;
     if (cudaMemcpyAsync(&hW, g->wpre + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(hacc, acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hWr, g->wpre_rev + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hacc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "wedge count readback: %s", cudaGetErrorString(cudaGetLastError())); break; }
+    if (hW != hWr) { st = fail(PB_ERR_CUDA, "wedge totals disagree (%llu vs %llu)", (unsigned long long)hW, (unsigned long long)hWr); break; }
     g->W = hW;
     g->maxw = hacc[0];
+    g->maxw_rev = hacc[1];
     g->rank_kind = rank_of ? 3 : kind;
   } while (0);
   dfree(keys, s); dfree(vals, s); dfree(tmp, s); dfree(drank, s); dfree(acc, s); dfree(wc, s);

@@ -26,12 +26,16 @@ def pb():
     return pb
 
 
-def _gpu_all(pb, g, kind, agg, rank_of=None, scratch=0):
+RETRIEVALS = ["low", "high"]
+
+
+def _gpu_all(pb, g, kind, agg, rank_of=None, scratch=0, retrieval="auto"):
     G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v)
     if rank_of is not None:
         G.rank_custom(rank_of)
     else:
         G.rank(kind)
+    G.set_retrieval(retrieval)
     c = G.count_all(agg, scratch_bytes=scratch)
     W = G.wedges
     ranks = G.ranks()
@@ -50,8 +54,8 @@ def test_fig2_worked_example(pb, fig2):
     nU, nV, u, v, gid = fig2_graph(fig2)
     rk = fig2_rank(fig2, gid)
     ref = oracle.count(nU, nV, u, v, rank_of=rk)
-    for agg in AGGS:
-        c, W, ranks = _gpu_all(pb, synth.Graph(nU, nV, u, v), None, agg, rank_of=rk)
+    for agg, rt in [(a, r) for a in AGGS for r in RETRIEVALS]:
+        c, W, ranks = _gpu_all(pb, synth.Graph(nU, nV, u, v), None, agg, rank_of=rk, retrieval=rt)
         assert W == 6
         np.testing.assert_array_equal(ranks, rk)
         _assert_same(c, ref, nU)
@@ -63,8 +67,8 @@ def test_complete_bipartite(pb, a, b):
     g = synth.complete_bipartite(a, b)
     C2 = lambda x: x * (x - 1) // 2  # noqa: E731
     for kind in RANKS:
-        for agg in AGGS:
-            c, _, _ = _gpu_all(pb, g, kind, agg)
+        for agg, rt in [(x, r) for x in AGGS for r in RETRIEVALS]:
+            c, _, _ = _gpu_all(pb, g, kind, agg, retrieval=rt)
             assert c.global_count == C2(a) * C2(b)
             assert np.all(c.per_vertex_U == (a - 1) * C2(b))
             assert np.all(c.per_vertex_V == (b - 1) * C2(a))
@@ -76,8 +80,8 @@ def test_tiny_graphs_every_ranking_and_aggregation(pb):
         ref = oracle.count(g.nU, g.nV, g.u, g.v, kind="degree")
         for kind in RANKS + ["random"]:
             rk = random_rank(500 + i, g.nU + g.nV) if kind == "random" else None
-            for agg in AGGS:
-                c, W, ranks = _gpu_all(pb, g, kind, agg, rank_of=rk)
+            for agg, rt in [(x, r) for x in AGGS for r in RETRIEVALS]:
+                c, W, ranks = _gpu_all(pb, g, kind, agg, rank_of=rk, retrieval=rt)
                 _assert_same(c, ref, g.nU)
                 want_W = oracle.wedges(g.nU, g.nV, g.u, g.v, kind=kind if rk is None else "side", rank_of=rk)
                 assert W == want_W
@@ -133,9 +137,9 @@ def test_mid_graphs_all_combinations(pb, mid):
         ref = oracle.count(g.nU, g.nV, g.u, g.v, kind="degree")
         for kind in RANKS:
             W = oracle.wedges(g.nU, g.nV, g.u, g.v, kind=kind)
-            for agg in AGGS:
-                c, gW, _ = _gpu_all(pb, g, kind, agg)
-                assert gW == W, (g.name, kind, agg)
+            for agg, rt in [(x, r) for x in AGGS for r in RETRIEVALS]:
+                c, gW, _ = _gpu_all(pb, g, kind, agg, retrieval=rt)
+                assert gW == W, (g.name, kind, agg, rt)
                 _assert_same(c, ref, g.nU)
 
 
@@ -149,10 +153,13 @@ def test_small_scratch_budget_chunks_exactly(pb, mid):
     G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
     maxw = G.info().max_wedges_x1
     assert maxw * 40 < G.wedges * 40 // 4          # sort needs several chunks
-    for agg, budget in [("hist", 8 * n + 4096), ("batch", 8 * n + 4096), ("hash", 32 * n + 4096),
-                        ("sort", 40 * maxw + 4096), ("auto", 8 * n + 4096)]:
-        c = G.count_all(agg, scratch_bytes=budget)
-        _assert_same(c, ref, g.nU)
+    for rt in RETRIEVALS:
+        G.set_retrieval(rt)
+        for agg, budget in [("hist", 8 * n + 4096), ("batch", 8 * n + 4096), ("hash", 32 * n + 4096),
+                            ("sort", 40 * maxw + 4096), ("auto", 8 * n + 4096)]:
+            c = G.count_all(agg, scratch_bytes=budget)
+            _assert_same(c, ref, g.nU)
+    G.set_retrieval("low")
     with pytest.raises(pb.PBError) as ei:
         G.count_all("sort", scratch_bytes=maxw)
     assert ei.value.status == 4
