@@ -146,6 +146,41 @@ __device__ __forceinline__ uint32_t owner_span(const CArgs &a, uint32_t x) {
   return a.rev ? a.off[x + 1] - a.off[x] : a.degp[x];
 }
 
+// The same table with 16-bit counts, two per 32-bit word (cnt16 holds cap/2
+// words).  Only for owners whose wedge count, and so every group size d, is
+// below 2^16: the light tier.
+__device__ __forceinline__ void sh_add16(uint32_t *key, uint32_t *cnt16, int lg, uint32_t x,
+                                         unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t h = hash_home(x, lg);
+  for (uint32_t probe = 0;; probe++) {
+    if (probe > mask) { atomicOr(err, 1ull); return; }
+    uint32_t k = reinterpret_cast<volatile uint32_t *>(key)[h];
+    if (k == x) break;
+    if (k == EMPTY) {
+      uint32_t prev = atomicCAS(&key[h], EMPTY, x);
+      if (prev == EMPTY || prev == x) break;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicAdd(&cnt16[h >> 1], 1u << ((h & 1u) << 4));
+}
+
+__device__ __forceinline__ uint32_t cnt16_at(const uint32_t *cnt16, uint32_t h) {
+  return (cnt16[h >> 1] >> ((h & 1u) << 4)) & 0xffffu;
+}
+
+__device__ __forceinline__ uint32_t sh_get16(const uint32_t *key, const uint32_t *cnt16, int lg, uint32_t x,
+                                             unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t h = hash_home(x, lg);
+  for (uint32_t probe = 0; key[h] != x; probe++) {
+    if (probe > mask) { atomicOr(err, 2ull); return 0; }
+    h = (h + 1) & mask;
+  }
+  return cnt16_at(cnt16, h);
+}
+
 __device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1, int rev) {
   uint64_t dmax = distinct_bound(wc, n, nU, x1, rev);
   int lg = 5;
@@ -191,14 +226,18 @@ __device__ __forceinline__ void warp_run_add(unsigned long long *acc, uint32_t k
 }
 
 // ---------------------------------------------------------------------------
-// Light tier: one warp per first endpoint.
+// Light tier: one warp per owner; per-warp table with 16-bit counts; LW_BATCH
+// steps of 32 wedges in flight per warp.
+constexpr int LW_BATCH = 4;
+
 template <bool PV, bool PE>
 __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *__restrict__ list,
                                                       uint32_t nlist) {
-  extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP counts
+  extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP / 2 count words
   __shared__ unsigned long long s_sum[LW_WARPS][32];
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-  uint32_t *key = dsm + w * 2 * LW_CAP, *cnt = key + LW_CAP;
+  uint32_t *key = dsm + w * (LW_CAP + LW_CAP / 2), *cnt = key + LW_CAP;
+  unsigned long long *err = &a.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[w][lane] = 0;
   for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
@@ -206,7 +245,8 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
-    for (uint32_t t = lane; t < cap; t += 32) { key[t] = EMPTY; cnt[t] = 0; }
+    for (uint32_t t = lane; t < cap; t += 32) key[t] = EMPTY;
+    for (uint32_t t = lane; t < cap / 2; t += 32) cnt[t] = 0;
     __syncwarp();
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
@@ -215,11 +255,18 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
       uint32_t y, c, oy;
       owner_nbr(a, base, i, v, y, c, oy);
       const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
-      for (uint32_t wb = 0; wb < tot; wb += 32) {
-        const uint32_t wi = wb + lane;
-        uint32_t src, slot;
-        warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
-        if (wi < tot) sh_add(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
+      for (uint32_t wb = 0; wb < tot; wb += LW_BATCH * 32) {
+        uint32_t x2v[LW_BATCH];
+#pragma unroll
+        for (int q = 0; q < LW_BATCH; q++) {
+          const uint32_t wi = wb + q * 32 + lane;
+          uint32_t src, slot;
+          warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
+          x2v[q] = wi < tot ? a.adj[slot] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < LW_BATCH; q++)
+          if (wb + q * 32 + lane < tot) sh_add16(key, cnt, lg, x2v[q], err);
       }
     }
     __syncwarp();
@@ -227,7 +274,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
     for (uint32_t t = lane; t < cap; t += 32) {
       uint32_t k = key[t];
       if (k != EMPTY) {
-        unsigned long long d = cnt[t], b = d * (d - 1) / 2;
+        unsigned long long d = cnt16_at(cnt, t), b = d * (d - 1) / 2;
         own += b;
         if (PV && b) atomicAdd(&a.pv[k], b);
       }
@@ -244,19 +291,23 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
         uint32_t y, c, oy;
         owner_nbr(a, base, i, v, y, c, oy);
         const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
-        for (uint32_t wb = 0; wb < tot; wb += 32) {
-          const uint32_t wi = wb + lane;
-          uint32_t src, slot;
-          warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
-          unsigned long long t = 0;
-          if (wi < tot) {
-            uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
-            if (d > 1) {
-              t = d - 1;
-              if (PE) atomicAdd(&a.es[slot], t);
-            }
+        for (uint32_t wb = 0; wb < tot; wb += LW_BATCH * 32) {
+          uint32_t x2v[LW_BATCH], srcv[LW_BATCH], slv[LW_BATCH], dv[LW_BATCH];
+#pragma unroll
+          for (int q = 0; q < LW_BATCH; q++) {
+            const uint32_t wi = wb + q * 32 + lane;
+            warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, srcv[q], slv[q]);
+            x2v[q] = wi < tot ? a.adj[slv[q]] : 0;
           }
-          warp_run_add(s_sum[w], src, t);
+#pragma unroll
+          for (int q = 0; q < LW_BATCH; q++)
+            dv[q] = wb + q * 32 + lane < tot ? sh_get16(key, cnt, lg, x2v[q], err) : 0;
+#pragma unroll
+          for (int q = 0; q < LW_BATCH; q++) {
+            unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
+            if (PE && t) atomicAdd(&a.es[slv[q]], t);
+            warp_run_add(s_sum[w], srcv[q], t);
+          }
         }
         __syncwarp();
         if (v) {
@@ -958,7 +1009,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
                    nh = static_cast<uint32_t>(hcnt[ACC_NHEAVY]);
     if (nl) {
       PhaseScope ph(PB_PHASE_LIGHT, s);
-      const size_t smem = 2 * LW_WARPS * LW_CAP * sizeof(uint32_t);
+      const size_t smem = LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t);
       PB_CUDA(cudaFuncSetAttribute(k_light<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_light<PV, PE>, LW_THREADS, smem);
