@@ -72,7 +72,9 @@ def _load():
                                        ctypes.c_int, u32p, u64p]
             lib.orc_edge_eq2.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, u32p,
                                          u32p, ctypes.c_uint64, u64p, ctypes.c_int, u64p]
-            for f in (lib.orc_rank, lib.orc_count, lib.orc_wedges, lib.orc_edge_eq2):
+            lib.orc_vertex_eq1.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, u32p,
+                                           u32p, ctypes.c_uint64, u64p, u64p]
+            for f in (lib.orc_rank, lib.orc_count, lib.orc_wedges, lib.orc_edge_eq2, lib.orc_vertex_eq1):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -166,3 +168,15 @@ def edge_eq2(nU: int, nV: int, u, v, query) -> np.ndarray:
     _check(lib.orc_edge_eq2(nU, nV, u.shape[0], pu, pv_, q.shape[0], _u64(q), 1, _u64(out)),
            "orc_edge_eq2")
     return out
+
+
+def vertex_eq1(nU: int, nV: int, u, v, query) -> np.ndarray:
+    """Per-vertex butterfly counts of the global ids `query` straight from Eq. 1."""
+    lib = _load()
+    u, pu = _u32(u)
+    v, pv_ = _u32(v)
+    q = np.ascontiguousarray(query, dtype=np.uint64)
+    out = np.zeros(q.shape[0], np.uint64)
+    _check(lib.orc_vertex_eq1(nU, nV, u.shape[0], pu, pv_, q.shape[0], _u64(q), _u64(out)), "orc_vertex_eq1")
+    return out
+

@@ -456,3 +456,54 @@ int orc_edge_eq2(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, con
   free(voff); free(vadj); bgraph_free(&g);
   return rc;
 }
+
+/* Eq. 1 evaluated directly for selected vertices (global ids), no ranking:
+ * count(x) = sum over x' != x on x's side of C(|N(x) n N(x')|, 2); the
+ * intersection sizes come from walking every 2-path x - y - x'. */
+int orc_vertex_eq1(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const uint32_t *v,
+                   uint64_t nq, const uint64_t *query, uint64_t *out) {
+  bgraph_t g;
+  int rc = bgraph_build(nU, nV, m_in, u, v, &g);
+  if (rc) return rc;
+  uint64_t n = (uint64_t)nU + nV;
+  /* adjacency of both sides by global id */
+  uint64_t *off = (uint64_t *)calloc(n + 1, sizeof(uint64_t));
+  uint32_t *nb = (uint32_t *)malloc(sizeof(uint32_t) * (2 * g.m + 1));
+  uint64_t *cur = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
+  uint32_t *cnt = (uint32_t *)calloc(n ? n : 1, sizeof(uint32_t));
+  uint32_t *touched = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+  if (!off || !nb || !cur || !cnt || !touched) {
+    free(off); free(nb); free(cur); free(cnt); free(touched); bgraph_free(&g);
+    return ORC_ERR_NOMEM;
+  }
+  for (uint64_t x = 0; x < n; x++) off[x + 1] = off[x] + g.deg[x];
+  memcpy(cur, off, sizeof(uint64_t) * (n + 1));
+  for (uint32_t i = 0; i < nU; i++)
+    for (uint64_t e = g.uoff[i]; e < g.uoff[i + 1]; e++) {
+      uint32_t j = nU + g.uadj[e];
+      nb[cur[i]++] = j;
+      nb[cur[j]++] = i;
+    }
+  for (uint64_t q = 0; q < nq && rc == ORC_OK; q++) {
+    uint64_t x = query[q];
+    if (x >= n) { rc = ORC_ERR_INVALID; break; }
+    uint64_t nt = 0, tot = 0;
+    for (uint64_t a = off[x]; a < off[x + 1]; a++) {
+      uint32_t y = nb[a];
+      for (uint64_t b = off[y]; b < off[y + 1]; b++) {
+        uint32_t x2 = nb[b];
+        if (x2 == x) continue;
+        if (cnt[x2]++ == 0) touched[nt++] = x2;
+      }
+    }
+    for (uint64_t t = 0; t < nt; t++) {
+      uint64_t c = cnt[touched[t]];
+      tot += c * (c - 1) / 2;
+      cnt[touched[t]] = 0;
+    }
+    out[q] = tot;
+  }
+  free(off); free(nb); free(cur); free(cnt); free(touched); bgraph_free(&g);
+  return rc;
+}
+

@@ -104,6 +104,13 @@ def test_oracle_matches_brute_force_on_tiny_graphs(tiny):
             assert oracle.wedges(g.nU, g.nV, g.u, g.v, rank_of=rk) == bw
 
 
+def test_eq1_direct_matches_brute(tiny):
+    for g in tiny[:20]:
+        _, pv, _ = brute.counts(g.nU, g.nV, g.u, g.v)
+        q = np.arange(g.nU + g.nV, dtype=np.uint64)
+        np.testing.assert_array_equal(oracle.vertex_eq1(g.nU, g.nV, g.u, g.v, q).astype(np.int64), pv)
+
+
 def test_eq2_direct_matches_brute(tiny):
     for g in tiny[:20]:
         _, _, pe = brute.counts(g.nU, g.nV, g.u, g.v)
