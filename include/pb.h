@@ -169,11 +169,42 @@ pb_status pb_count_all(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t
                        uint64_t *out_U, uint64_t *out_V, uint64_t *out_E, int out_on_device,
                        void *stream);
 
+/* Counts restricted to the wedges owned by labels in [owner_lo, owner_hi)
+ * (labels: U vertices [0, nU), V vertices [nU, nU + nV), each side in rank
+ * order; the owner is the endpoint pb_set_retrieval selects).  The outer loop
+ * of Algorithm 2 is over independent owners, so the outputs of a partition of
+ * [0, n) into ranges sum, element by element, to those of pb_count_all: a
+ * graph can be split over devices or processes this way and the parts added.
+ * Outputs as for pb_count_all (partial counts). */
+pb_status pb_count_owner_range(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint32_t owner_lo,
+                               uint32_t owner_hi, uint64_t *out_global, uint64_t *out_U,
+                               uint64_t *out_V, uint64_t *out_E, int out_on_device, void *stream);
+
+/* Exclusive prefix sum over labels of the wedges each owner holds under the
+ * current retrieval: out[n + 1] uint64 (host or device).  out[n] = W.  Input
+ * for splitting the owners into ranges of equal wedge mass. */
+pb_status pb_wedge_prefix(const pb_graph *g, uint64_t *out, int out_on_device, void *stream);
+
 /* Number of wedges Algorithm 2 retrieves under the current ranking. */
 pb_status pb_wedge_count(const pb_graph *g, uint64_t *W);
 
 /* Statistics of the graph (host struct). */
 pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info);
+
+/* Sparsification for approximate total counts (Sec. "Approximate counting").
+ *  EDGE:  keep each edge with probability p; the total butterfly count of the
+ *         kept graph divided by p^4 is an unbiased estimate of the total.
+ *  COLOR: colourful sparsification: each vertex gets one of ceil(1/p) colours,
+ *         edges whose two endpoints share a colour are kept; divide by p^3.
+ * Decisions hash the pair (u, v) or the vertex (SplitMix64's output function,
+ * seeded), so duplicate pairs share one decision and results are
+ * reproducible.  Writes the kept pairs, in input order, to out_u / out_v
+ * (m entries of room; host or device as on_device) and their number to
+ * *out_m (host).  Build a graph from them with pb_graph_from_edges. */
+typedef enum { PB_SPARSIFY_EDGE = 0, PB_SPARSIFY_COLOR = 1 } pb_sparsify_kind;
+pb_status pb_sparsify(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v,
+                      int on_device, pb_sparsify_kind kind, double p, uint64_t seed, uint32_t *out_u,
+                      uint32_t *out_v, uint64_t *out_m, void *stream);
 
 /* Releases the graph and every device buffer it holds.  NULL is accepted. */
 pb_status pb_graph_free(pb_graph *g);

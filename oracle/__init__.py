@@ -72,6 +72,13 @@ def _load():
                                        ctypes.c_int, u32p, u64p]
             lib.orc_edge_eq2.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, u32p,
                                          u32p, ctypes.c_uint64, u64p, ctypes.c_int, u64p]
+            lib.orc_count_range.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, u32p, u32p,
+                                            ctypes.c_int, u32p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                            u64p, u64p, u64p, u64p, u64p]
+            lib.orc_owner_wedges.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, u32p, u32p,
+                                             ctypes.c_int, u32p, u64p]
+            lib.orc_count_range.restype = ctypes.c_int
+            lib.orc_owner_wedges.restype = ctypes.c_int
             lib.orc_vertex_eq1.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, u32p,
                                            u32p, ctypes.c_uint64, u64p, u64p]
             for f in (lib.orc_rank, lib.orc_count, lib.orc_wedges, lib.orc_edge_eq2, lib.orc_vertex_eq1):
@@ -178,5 +185,34 @@ def vertex_eq1(nU: int, nV: int, u, v, query) -> np.ndarray:
     q = np.ascontiguousarray(query, dtype=np.uint64)
     out = np.zeros(q.shape[0], np.uint64)
     _check(lib.orc_vertex_eq1(nU, nV, u.shape[0], pu, pv_, q.shape[0], _u64(q), _u64(out)), "orc_vertex_eq1")
+    return out
+
+
+def count_range(nU: int, nV: int, u, v, x_lo: int, x_hi: int, kind: str | int = "degree",
+                nthreads: int | None = None) -> Counts:
+    """Partial counts of the wedges whose first endpoint has rank in [x_lo, x_hi)."""
+    lib = _load()
+    k = RANK_KINDS[kind] if isinstance(kind, str) else int(kind)
+    u, pu = _u32(u)
+    v, pv_ = _u32(v)
+    m_in = u.shape[0]
+    W = np.zeros(1, np.uint64)
+    g = np.zeros(1, np.uint64)
+    m = np.zeros(1, np.uint64)
+    pvo = np.zeros(nU + nV, np.uint64)
+    peo = np.zeros(m_in, np.uint64)
+    _check(lib.orc_count_range(nU, nV, m_in, pu, pv_, k, None, nthreads or threads(), x_lo, x_hi, _u64(W), _u64(g),
+                               _u64(pvo), _u64(peo), _u64(m)), "orc_count_range")
+    return Counts(nU, int(W[0]), int(g[0]), int(m[0]), pvo, peo)
+
+
+def owner_wedges(nU: int, nV: int, u, v, kind: str | int = "degree") -> np.ndarray:
+    """Wedges retrieved by each first endpoint, indexed by rank."""
+    lib = _load()
+    k = RANK_KINDS[kind] if isinstance(kind, str) else int(kind)
+    u, pu = _u32(u)
+    v, pv_ = _u32(v)
+    out = np.zeros(nU + nV, np.uint64)
+    _check(lib.orc_owner_wedges(nU, nV, u.shape[0], pu, pv_, k, None, _u64(out)), "orc_owner_wedges")
     return out
 

@@ -228,6 +228,7 @@ static inline uint64_t prefix_above(const rgraph_t *r, uint64_t x, uint32_t t) {
 typedef struct {
   const rgraph_t *r;
   uint64_t *next;       /* shared x1 cursor */
+  uint64_t hi;          /* first x1 not counted */
   uint64_t *pv;         /* n, rank space, or NULL */
   uint64_t *pe;         /* m, canonical edge ids, or NULL */
   unsigned __int128 global;
@@ -245,8 +246,8 @@ static void *count_worker(void *arg) {
   if (!A || !touched) { free(A); free(touched); j->wedges = ~0ULL; return NULL; }
   for (;;) {
     uint64_t lo = __atomic_fetch_add(j->next, X1_CHUNK, __ATOMIC_RELAXED);
-    if (lo >= n) break;
-    uint64_t hi = lo + X1_CHUNK < n ? lo + X1_CHUNK : n;
+    if (lo >= j->hi) break;
+    uint64_t hi = lo + X1_CHUNK < j->hi ? lo + X1_CHUNK : j->hi;
     for (uint64_t x1 = lo; x1 < hi; x1++) {
       uint64_t nt = 0;
       uint64_t s1 = r->off[x1], k1 = prefix_above(r, x1, (uint32_t)x1);
@@ -292,16 +293,16 @@ static void *count_worker(void *arg) {
   return NULL;
 }
 
-static int run_count(const rgraph_t *r, int nthreads, uint64_t *W, unsigned __int128 *global,
-                     uint64_t *pv_rank, uint64_t *pe) {
+static int run_count(const rgraph_t *r, int nthreads, uint64_t x_lo, uint64_t x_hi, uint64_t *W,
+                     unsigned __int128 *global, uint64_t *pv_rank, uint64_t *pe) {
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 512) nthreads = 512;
-  uint64_t next = 0;
+  uint64_t next = x_lo;
   cnt_job_t *jobs = (cnt_job_t *)calloc((size_t)nthreads, sizeof(cnt_job_t));
   pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
   if (!jobs || !th) { free(jobs); free(th); return ORC_ERR_NOMEM; }
   for (int t = 0; t < nthreads; t++) {
-    jobs[t].r = r; jobs[t].next = &next; jobs[t].pv = pv_rank; jobs[t].pe = pe;
+    jobs[t].r = r; jobs[t].next = &next; jobs[t].hi = x_hi; jobs[t].pv = pv_rank; jobs[t].pe = pe;
   }
   for (int t = 1; t < nthreads; t++) pthread_create(&th[t], NULL, count_worker, &jobs[t]);
   count_worker(&jobs[0]);
@@ -340,9 +341,25 @@ int orc_rank(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const u
  *   pv_out[n]    per-vertex counts by global id (U then V);
  *   pe_out[m_in] per-edge counts in input order (duplicates share their edge's);
  *   m_out        number of distinct edges. */
+/* As orc_count, restricted to first endpoints with rank in [x_lo, x_hi): the
+ * partial counts of those wedges (Algorithm 2's outer loop is over
+ * independent first endpoints, so the parts of a partition add up). */
+int orc_count_range(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const uint32_t *v,
+                    int kind, const uint32_t *rank_in, int nthreads, uint64_t x_lo, uint64_t x_hi,
+                    uint64_t *W_out, uint64_t *global_out, uint64_t *pv_out, uint64_t *pe_out,
+                    uint64_t *m_out);
+
 int orc_count(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const uint32_t *v,
               int kind, const uint32_t *rank_in, int nthreads, uint64_t *W_out,
               uint64_t *global_out, uint64_t *pv_out, uint64_t *pe_out, uint64_t *m_out) {
+  return orc_count_range(nU, nV, m_in, u, v, kind, rank_in, nthreads, 0, UINT64_MAX, W_out, global_out,
+                         pv_out, pe_out, m_out);
+}
+
+int orc_count_range(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const uint32_t *v,
+                    int kind, const uint32_t *rank_in, int nthreads, uint64_t x_lo, uint64_t x_hi,
+                    uint64_t *W_out, uint64_t *global_out, uint64_t *pv_out, uint64_t *pe_out,
+                    uint64_t *m_out) {
   bgraph_t g;
   int rc = bgraph_build(nU, nV, m_in, u, v, &g);
   if (rc) return rc;
@@ -374,7 +391,9 @@ int orc_count(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const 
   }
   uint64_t W = 0;
   unsigned __int128 glob = 0;
-  rc = run_count(&r, nthreads, &W, &glob, pv_rank, pe);
+  if (x_hi > n) x_hi = n;
+  if (x_lo > x_hi) x_lo = x_hi;
+  rc = run_count(&r, nthreads, x_lo, x_hi, &W, &glob, pv_rank, pe);
   if (rc == ORC_OK) {
     if (glob > (unsigned __int128)UINT64_MAX) rc = ORC_ERR_OVERFLOW;
     if (W_out) *W_out = W;
@@ -410,6 +429,29 @@ int orc_wedges(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const
     }
   }
   *W_out = W;
+  rgraph_free(&r); free(rank); bgraph_free(&g);
+  return ORC_OK;
+}
+
+/* Wedges of each first endpoint, by rank: wx[r] for r in [0, n). */
+int orc_owner_wedges(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const uint32_t *v,
+                     int kind, const uint32_t *rank_in, uint64_t *wx) {
+  bgraph_t g;
+  int rc = bgraph_build(nU, nV, m_in, u, v, &g);
+  if (rc) return rc;
+  uint64_t n = (uint64_t)nU + nV;
+  uint32_t *rank = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+  if (!rank) { bgraph_free(&g); return ORC_ERR_NOMEM; }
+  if (rank_in) memcpy(rank, rank_in, sizeof(uint32_t) * n);
+  else if ((rc = make_rank(&g, kind, rank)) != ORC_OK) { free(rank); bgraph_free(&g); return rc; }
+  rgraph_t r;
+  rc = preprocess(&g, rank, &r);
+  if (rc) { free(rank); bgraph_free(&g); return rc; }
+  for (uint64_t x = 0; x < n; x++) {
+    uint64_t k1 = prefix_above(&r, x, (uint32_t)x), w = 0;
+    for (uint64_t i = 0; i < k1; i++) w += prefix_above(&r, r.nbr[r.off[x] + i], (uint32_t)x);
+    wx[x] = w;
+  }
   rgraph_free(&r); free(rank); bgraph_free(&g);
   return ORC_OK;
 }

@@ -35,7 +35,7 @@ ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ran
                "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
                "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string",
                "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc",
-               "pb_set_retrieval"]
+               "pb_set_retrieval", "pb_count_owner_range", "pb_wedge_prefix", "pb_sparsify"]
 
 PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
@@ -107,6 +107,12 @@ def load_library(path: str = LIB_PATH):
         lib.pb_count_noalloc.restype = i32
         lib.pb_set_retrieval.argtypes = [vp, i32]
         lib.pb_set_retrieval.restype = i32
+        lib.pb_count_owner_range.argtypes = [vp, i32, u64, u32, u32, u64p, vp, vp, vp, i32, vp]
+        lib.pb_count_owner_range.restype = i32
+        lib.pb_wedge_prefix.argtypes = [vp, vp, i32, vp]
+        lib.pb_wedge_prefix.restype = i32
+        lib.pb_sparsify.argtypes = [u32, u32, u64, vp, vp, i32, i32, ctypes.c_double, u64, vp, vp, u64p, vp]
+        lib.pb_sparsify.restype = i32
         _lib = lib
         return lib
 
@@ -172,6 +178,40 @@ def count_noalloc(n: int, nU: int, off, adj, cpos, degp, out_global, out_pv=None
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
     _check(lib.pb_count_noalloc(n, nU, p(off), p(adj), p(cpos), p(degp), p(out_global), p(out_pv),
                                 _stream(stream)))
+
+
+SPARSIFY = {"edge": 0, "color": 1}
+
+
+def sparsify(nU: int, nV: int, u, v, kind: str, p: float, seed: int, stream=None):
+    """Kept edge pairs (host uint32 arrays) of edge or colourful
+    sparsification, and the scale 1/p^4 or 1/p^3 for the estimate."""
+    lib = load_library()
+    torch = _torch()
+    pu, du, ku = _edge_arg(u, torch)
+    pv, dv, kv = _edge_arg(v, torch)
+    if du:
+        raise ValueError("pass host arrays")
+    m = int(ku.shape[0])
+    ou = np.empty(max(m, 1), np.uint32)
+    ov = np.empty(max(m, 1), np.uint32)
+    om = ctypes.c_uint64()
+    _check(lib.pb_sparsify(nU, nV, m, pu, pv, 0, SPARSIFY[kind], p, seed, ctypes.c_void_p(ou.ctypes.data),
+                           ctypes.c_void_p(ov.ctypes.data), ctypes.byref(om), _stream(stream)))
+    k = int(om.value)
+    scale = 1.0 / p ** 4 if kind == "edge" else 1.0 / p ** 3
+    return ou[:k].copy(), ov[:k].copy(), scale
+
+
+def approx_global(nU: int, nV: int, u, v, kind: str = "edge", p: float = 0.5, seed: int = 1,
+                  agg: str = "auto") -> float:
+    """Approximate total butterfly count: exact count of the sparsified graph,
+    scaled (Sec. "Approximate counting")."""
+    su, sv, scale = sparsify(nU, nV, u, v, kind, p, seed)
+    G = Graph.from_edges(nU, nV, su, sv).rank("degree")
+    c = G.count_global(agg)
+    G.free()
+    return c * scale
 
 
 @dataclass
@@ -271,8 +311,16 @@ class Graph:
         return self.count_all(agg, scratch_bytes, glob=False, vertex=False, edge=True, on_device=on_device,
                               stream=stream).per_edge
 
+    def wedge_prefix(self, stream=None) -> np.ndarray:
+        """Per-owner exclusive wedge prefix (n + 1 uint64) under the current
+        retrieval; the last entry is W."""
+        out = np.empty(self.nU + self.nV + 1, np.uint64)
+        _check(load_library().pb_wedge_prefix(self._h, ctypes.c_void_p(out.ctypes.data), 0, _stream(stream)))
+        return out
+
     def count_all(self, agg: str = "auto", scratch_bytes: int = 0, glob: bool = True, vertex: bool = True,
-                  edge: bool = True, on_device: bool = False, out=None, stream=None) -> Counts:
+                  edge: bool = True, on_device: bool = False, out=None, stream=None,
+                  owners: tuple[int, int] | None = None) -> Counts:
         """One wedge pass producing any of the three outputs.  Host outputs are
         uint64 numpy arrays; device outputs are int64 CUDA tensors holding the
         uint64 bit patterns (``out`` may pass preallocated ones as a dict)."""
@@ -302,6 +350,11 @@ class Graph:
                 if isinstance(a, torch.Tensor):   # e.g. pinned host buffers
                     return ctypes.c_void_p(a.data_ptr())
                 return ctypes.c_void_p(a.ctypes.data)
-        _check(lib.pb_count_all(self._h, AGGS[agg], scratch_bytes, ctypes.byref(g) if g is not None else None,
-                                ptr(U), ptr(V), ptr(E), int(on_device), _stream(stream)))
+        if owners is None:
+            _check(lib.pb_count_all(self._h, AGGS[agg], scratch_bytes, ctypes.byref(g) if g is not None else None,
+                                    ptr(U), ptr(V), ptr(E), int(on_device), _stream(stream)))
+        else:
+            _check(lib.pb_count_owner_range(self._h, AGGS[agg], scratch_bytes, int(owners[0]), int(owners[1]),
+                                            ctypes.byref(g) if g is not None else None, ptr(U), ptr(V), ptr(E),
+                                            int(on_device), _stream(stream)))
         return Counts(int(g.value) if g is not None else None, U, V, E)

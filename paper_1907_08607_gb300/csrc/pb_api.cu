@@ -326,6 +326,40 @@ pb_status pb_count_all(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t
   return st;
 }
 
+pb_status pb_count_owner_range(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint32_t owner_lo,
+                               uint32_t owner_hi, uint64_t *out_global, uint64_t *out_U, uint64_t *out_V,
+                               uint64_t *out_E, int out_on_device, void *stream) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  if (owner_lo > owner_hi || owner_hi > g->n) return fail(PB_ERR_INVALID, "owner range [%u, %u) outside [0, %llu)",
+                                                           owner_lo, owner_hi, (unsigned long long)g->n);
+  DeviceGuard dg(g->device);
+  CountOut o;
+  o.global = out_global;
+  o.U = out_U;
+  o.V = out_V;
+  o.E = out_E;
+  o.on_device = out_on_device;
+  o.owner_lo = owner_lo;
+  o.owner_hi = owner_hi;
+  pb_status st = count_all(g, static_cast<int>(agg), scratch_bytes, o, static_cast<cudaStream_t>(stream));
+  prof_flush();
+  return st;
+}
+
+pb_status pb_wedge_prefix(const pb_graph *g, uint64_t *out, int out_on_device, void *stream) {
+  clear_error();
+  if (!g || !out) return fail(PB_ERR_INVALID, "graph or out is NULL");
+  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t *src = g->retrieval == PB_RETRIEVE_LOW ? g->wpre : g->wpre_rev;
+  PB_CUDA(cudaMemcpyAsync(out, src, (g->n + 1) * sizeof(uint64_t),
+                          out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  PB_CUDA(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
 pb_status pb_count_global(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_t *out, void *stream) {
   if (!out) return fail(PB_ERR_INVALID, "out is NULL");
   return pb_count_all(g, agg, scratch_bytes, out, nullptr, nullptr, nullptr, 0, stream);

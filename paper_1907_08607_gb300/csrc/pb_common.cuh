@@ -148,6 +148,7 @@ struct CountOut {
   uint64_t *global = nullptr;  // host
   uint64_t *U = nullptr, *V = nullptr, *E = nullptr;
   int on_device = 0;
+  uint64_t owner_lo = 0, owner_hi = UINT64_MAX;  // owners (labels) whose wedges are counted
 };
 pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut &o,
                     cudaStream_t s);

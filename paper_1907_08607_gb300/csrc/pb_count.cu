@@ -839,14 +839,15 @@ __global__ void k_chunk_end(const uint64_t *__restrict__ wpre, uint64_t n, uint3
 
 // ---------------------------------------------------------------------------
 // Tier classification.
-__global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64_t light_max, uint64_t med_max,
+__global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64_t olo, uint64_t ohi,
+                           uint64_t light_max, uint64_t med_max,
                            uint64_t hub_min, uint32_t *__restrict__ light, uint32_t *__restrict__ med,
                            uint64_t *__restrict__ heavy_keys, int bitsN, unsigned long long *acc) {
   size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   size_t iters = (n + stride - 1) / stride;
   for (size_t itn = 0; itn < iters; itn++) {
     size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x + itn * stride;
-    uint64_t wc = x < n ? wpre[x + 1] - wpre[x] : 0;
+    uint64_t wc = (x < n && x >= olo && x < ohi) ? wpre[x + 1] - wpre[x] : 0;
     int tier = wc == 0 ? 0 : (wc <= light_max ? 1 : (wc <= med_max ? 2 : 3));
     uint32_t hubs = __popc(__ballot_sync(FULL, tier == 3 && wc > hub_min));
     if (lane_id() == 0 && hubs) atomicAdd(&acc[ACC_NHUB], (unsigned long long)hubs);
@@ -974,6 +975,7 @@ struct Plan {
   unsigned cluster;   // blocks per heavy first endpoint
   uint64_t max_slots; // cap on concurrently processed hubs (0 = resident clusters)
   uint64_t hub_min;   // heavy first endpoints above this many wedges get a cluster each
+  uint64_t owner_lo, owner_hi;  // owners counted
 };
 
 // Tuning knobs (environment): PB_HEAVY_CLUSTER, PB_HEAVY_SLOTS, PB_HUB_MIN.
@@ -998,7 +1000,8 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
     if ((st = dalloc_t(&hkeys, n + 1, s)) != PB_OK) break;
     {
       PhaseScope ph(PB_PHASE_CLASSIFY, s);
-      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, p.light_max, p.med_max, p.hub_min, light, med,
+      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, p.owner_lo, p.owner_hi, p.light_max, p.med_max,
+                                                        p.hub_min, light, med,
                                                         hkeys, g->bitsN, a.acc);
       count_launch();
       ph.finish(s);
@@ -1101,7 +1104,8 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
 }
 
 template <bool PV, bool PE>
-static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, cudaStream_t s) {
+static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t olo, uint64_t ohi,
+                          cudaStream_t s) {
   const uint64_t n = g->n;
   const int bitsN = g->bitsN;
   // bytes per wedge: key, radix ping-pong key, head, run id, run key, run start, run d
@@ -1126,9 +1130,9 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, cudaStre
     if ((st = dalloc_t(&rstart, cap_alloc, s)) != PB_OK) break;
     if ((st = dalloc_t(&ud, cap_alloc, s)) != PB_OK) break;
     const int sms = sm_count(g->device);
-    uint32_t lo = 0;
-    while (lo < n && st == PB_OK) {
-      k_chunk_end<<<1, 1, 0, s>>>(a.wpre, n, lo, cap, dchunk);
+    uint32_t lo = static_cast<uint32_t>(olo);
+    while (lo < ohi && st == PB_OK) {
+      k_chunk_end<<<1, 1, 0, s>>>(a.wpre, ohi, lo, cap, dchunk);
       count_launch();
       unsigned long long hc[2];
       if (cudaMemcpyAsync(hc, dchunk, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1210,6 +1214,8 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     p.pe = want_pe;
     p.light_max = LIGHT_MAX;
     p.med_max = MED_MAX;
+    p.owner_lo = o.owner_lo < n ? o.owner_lo : n;
+    p.owner_hi = o.owner_hi < n ? o.owner_hi : n;
     p.dense = agg != PB_AGG_HASH;
     p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", 2));
     p.max_slots = env_u64("PB_HEAVY_SLOTS", 0);
@@ -1225,10 +1231,10 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     pb_status st;
     if (agg == PB_AGG_SORT) {
       PhaseScope ph(PB_PHASE_SORT, s);
-      if (want_pv && want_pe) st = run_sort<true, true>(g, a, budget, s);
-      else if (want_pv) st = run_sort<true, false>(g, a, budget, s);
-      else if (want_pe) st = run_sort<false, true>(g, a, budget, s);
-      else st = run_sort<false, false>(g, a, budget, s);
+      if (want_pv && want_pe) st = run_sort<true, true>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      else if (want_pv) st = run_sort<true, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      else if (want_pe) st = run_sort<false, true>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      else st = run_sort<false, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
       if (st == PB_OK) ph.finish(s, g->W);
     } else if (want_pv && want_pe) st = run_tiers<true, true>(g, a, p, budget, s);
     else if (want_pv) st = run_tiers<true, false>(g, a, p, budget, s);

@@ -212,3 +212,29 @@ def test_degenerate_inputs(pb):
     with pytest.raises(pb.PBError):
         G.rank_custom(np.array([0, 0, 1, 2], np.uint32))
     G.free()
+
+
+def test_virtual_shards_sum_to_the_whole(pb, mid):
+    """k owner ranges of equal wedge mass on one GPU: the partial counts add
+    up, element by element, to the unsharded count."""
+    from paper_1907_08607_gb300 import shard
+    g = mid[1]
+    ref = oracle.count(g.nU, g.nV, g.u, g.v, kind="degree")
+    G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
+    for rt in RETRIEVALS:
+        G.set_retrieval(rt)
+        pre = G.wedge_prefix()
+        assert int(pre[-1]) == G.wedges
+        for agg in ["auto", "sort"]:
+            for k in (1, 3, 8):
+                tot_g, pv, pe = 0, 0, 0
+                for lo, hi in shard.partition(pre, k):
+                    c = G.count_all(agg, owners=(lo, hi))
+                    tot_g += c.global_count
+                    pv = pv + np.concatenate([c.per_vertex_U, c.per_vertex_V])
+                    pe = pe + c.per_edge
+                assert tot_g == ref.global_count
+                np.testing.assert_array_equal(pv, ref.per_vertex)
+                np.testing.assert_array_equal(pe, ref.per_edge)
+    G.free()
+

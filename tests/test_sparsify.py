@@ -1,0 +1,71 @@
+"""Approximate counting by sparsification (Sec. "Approximate counting").
+
+CPU: the oracle's estimators are pinned by the probabilities the paper
+states (a butterfly survives edge sparsification with probability p^4 and
+colourful sparsification with p^3) -- exactly on single butterflies, and as a
+sample mean over many seeds on small graphs.  GPU: the device filter keeps
+exactly the oracle's edges, and the scaled exact count matches.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import brute
+from oracle import sparsify as osp
+
+
+def test_p_one_keeps_everything():
+    g = synth.workload(1)
+    for kind in ("edge", "color"):
+        u, v, scale = osp.sparsify(g.nU, g.nV, g.u, g.v, kind, 1.0, 7)
+        assert u.shape[0] == g.m and scale == 1.0
+
+
+@pytest.mark.parametrize("kind,p,power", [("edge", 0.5, 4), ("edge", 0.3, 4), ("color", 0.5, 3),
+                                          ("color", 0.25, 3)])
+def test_single_butterfly_survival_probability(kind, p, power):
+    """Over many seeds, one K_{2,2} survives with frequency ~ p^power."""
+    g = synth.complete_bipartite(2, 2)
+    seeds = 20000
+    kept = 0
+    for s in range(seeds):
+        m = osp.keep_mask(2, g.u, g.v, kind, p, 1000 + s)
+        kept += int(m.all())
+    want = p ** power
+    sd = math.sqrt(want * (1 - want) / seeds)
+    assert abs(kept / seeds - want) < 5 * sd
+
+
+@pytest.mark.parametrize("kind", ["edge", "color"])
+def test_estimator_is_unbiased_on_small_graphs(kind):
+    g = synth.er_graph(0x5A, 30, 40, 500)
+    exact = brute.global_count(g.nU, g.nV, g.u, g.v)
+    p = 0.5
+    est = []
+    for s in range(300):
+        u, v, scale = osp.sparsify(g.nU, g.nV, g.u, g.v, kind, p, 77 + s)
+        est.append(brute.global_count(g.nU, g.nV, u, v) * scale)
+    est = np.array(est)
+    assert abs(est.mean() - exact) < 5 * est.std() / math.sqrt(len(est))
+
+
+@pytest.mark.gpu
+def test_gpu_filter_keeps_the_oracle_edges_and_scales():
+    import paper_1907_08607_gb300 as pb
+    from paper_1907_08607_gb300 import build
+    build.build()
+    g = synth.chung_lu_graph(0xC0FFEE, 20_000, 60_000, 400_000, 2.1, 2.5, cap_u=3000, cap_v=3000)
+    d = synth.with_duplicates(g, seed=9, frac=0.1)
+    for kind, p in [("edge", 0.5), ("edge", 0.2), ("color", 0.5), ("color", 0.1)]:
+        for seed in (1, 123456789):
+            gu, gv, gs = pb.sparsify(d.nU, d.nV, d.u, d.v, kind, p, seed)
+            ou, ov, os_ = osp.sparsify(d.nU, d.nV, d.u, d.v, kind, p, seed)
+            np.testing.assert_array_equal(gu, ou)
+            np.testing.assert_array_equal(gv, ov)
+            assert gs == os_
+            est = pb.approx_global(d.nU, d.nV, d.u, d.v, kind, p, seed)
+            want = oracle.count(d.nU, d.nV, ou, ov, per_vertex=False, per_edge=False).global_count * os_
+            assert est == want
