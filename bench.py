@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "serving"],
+                    help="plain: one graph per step (default); batched: 1,024 graphs in one CUDA-graph launch "
+                         "vs one launch per graph; serving: Poisson request stream")
+    ap.add_argument("--graphs", type=int, default=1024)
     ap.add_argument("--workload", default="cl2", choices=sorted(WORKLOADS))
     ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree"])
     ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
@@ -348,10 +352,102 @@ def run_gb300(args):
     return 0
 
 
+def run_serving(args):
+    from paper_1907_08607_gb300 import serve
+    print(json.dumps(serve.bench(args)), flush=True)
+    return 0
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
+
+
+def run_batched(args):
+    """Batched workload: graphs with m log-uniform in [1e3, 1e6], ER or
+    Chung-Lu by coin flip, |V|/|U| log-uniform in [0.1, 10]; global + per-vertex
+    counts.  Counting only (graphs built and ranked beforehand): one CUDA-graph
+    launch for the whole batch vs one pb_count_all per graph."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1907_08607_gb300 as pb
+    from paper_1907_08607_gb300 import build as pbuild
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    pb.load_library()
+    gs = [synth.batch_graph(i) for i in range(args.graphs)]
+    Gs = []
+    for g in gs:
+        G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
+        G.set_retrieval("auto")
+        Gs.append(G)
+    W = sum(G.wedges for G in Gs)
+    outs = [{"U": torch.empty(G.nU, dtype=torch.int64, device="cuda"),
+             "V": torch.empty(G.nV, dtype=torch.int64, device="cuda")} for G in Gs]
+    stream = torch.cuda.current_stream()
+
+    def plain_pass(lat=None):
+        for G, o in zip(Gs, outs):
+            t0 = time.perf_counter()
+            G.count_all("auto", edge=False, on_device=True, out=o)
+            if lat is not None:
+                lat.append(time.perf_counter() - t0)
+
+    B = pb.Batch(Gs, vertex=True)
+    for _ in range(max(3, args.warmup)):
+        plain_pass()
+        B.run()
+    torch.cuda.synchronize()
+    lat = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plain_pass(lat)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / args.steps
+    blat = []
+    l0 = pb.kernel_launches()
+    e0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        B.run()
+        blat.append(time.perf_counter() - t0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = pb.kernel_launches() - l0
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    glob = B.globals()
+    same = all(int(glob[i]) == G.count_global("auto") for i, G in enumerate(Gs[:64]))
+    line = {"metric": METRIC, "mode": "batched", "value": W / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": batch_ms, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{args.graphs} graphs, m log-uniform [1e3,1e6], ER or Chung-Lu (gamma 1.8-2.8), "
+                                   "|V|/|U| log-uniform [0.1,10]", "outputs": "global+per-vertex", "W": W,
+                       "edges": int(sum(g.m for g in gs)), "rank": "degree", "agg": "auto (autotuned)"},
+            "plain": {"value": W / (plain_ms / 1e3), "ms_per_pass": plain_ms,
+                      "per_graph_latency_ms": {"p50": 1e3 * _pct(lat, 50), "p99": 1e3 * _pct(lat, 99)}},
+            "batched_latency_ms": {"p50": 1e3 * _pct(blat, 50), "p99": 1e3 * _pct(blat, 99)},
+            "speedup_vs_plain": plain_ms / batch_ms, "gpu_launches": launches,
+            "results_equal_alone_and_in_batch": same}
+    print(json.dumps(line), flush=True)
+    B.free()
+    for G in Gs:
+        G.free()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "serving":
+        return run_serving(args)
     return run_gb300(args)
 
 

@@ -206,6 +206,47 @@ pb_status pb_sparsify(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, c
                       int on_device, pb_sparsify_kind kind, double p, uint64_t seed, uint32_t *out_u,
                       uint32_t *out_v, uint64_t *out_m, void *stream);
 
+/* Autotuner: a plan from the graph's degree and wedge statistics.
+ *  f_side = (W_side - W_rank) / W_side, W_side the wedges of side order (the
+ *  fewer of sum C(deg v, 2) over V and over U), W_rank those of the current
+ *  ranking: the paper's ranking-choice metric (Sec. "Experiments", Table 3);
+ *  side order is recommended when f_side < 0.1.
+ *  retrieval: the endpoint that gives the smaller largest per-owner wedge
+ *  count (load balance; the higher-ranked one almost always).
+ *  hub_min / hub_cluster: owners above hub_min wedges are given a cluster of
+ *  hub_cluster blocks (hub_min = UINT64_MAX when no owner needs one).
+ * pb_count_* with PB_AGG_AUTO and PB_RETRIEVE_AUTO follow this plan. */
+typedef struct {
+  int32_t rank_kind;    /* recommended pb_rank_kind */
+  int32_t retrieval;    /* pb_retrieval (LOW or HIGH) */
+  int32_t agg;          /* pb_agg */
+  uint32_t hub_cluster;
+  uint64_t hub_min;
+  double f_side;
+  uint64_t W_side, W_rank;
+  uint64_t max_owner_wedges;  /* under the chosen retrieval */
+} pb_plan_t;
+pb_status pb_autotune(const pb_graph *g, pb_plan_t *plan);
+
+/* Batched counting: many ranked graphs counted by one persistent kernel per
+ * work tier over all their owners, the launches captured once in a CUDA
+ * graph and replayed by every pb_batch_run (global and, with want_vertex,
+ * per-vertex counts).  Each graph's owner direction follows pb_autotune.
+ * The graphs must stay alive and unchanged while the batch exists.
+ * scratch_bytes bounds the shared dense-histogram slots (0 = 16 GiB). */
+typedef struct pb_batch pb_batch;
+pb_status pb_batch_create(pb_graph *const *graphs, uint32_t ng, int want_vertex, uint64_t scratch_bytes,
+                          void *stream, pb_batch **out);
+pb_status pb_batch_run(pb_batch *b, void *stream);
+/* out[ng] host: global count of each graph after the last run. */
+pb_status pb_batch_globals(const pb_batch *b, uint64_t *out, void *stream);
+/* Per-vertex counts of graph i after the last run (as pb_count_vertex). */
+pb_status pb_batch_vertex(const pb_batch *b, uint32_t i, uint64_t *out_U, uint64_t *out_V, int out_on_device,
+                          void *stream);
+/* Total wedges of all graphs in the batch (under their chosen owners). */
+pb_status pb_batch_wedges(const pb_batch *b, uint64_t *W);
+pb_status pb_batch_free(pb_batch *b);
+
 /* Releases the graph and every device buffer it holds.  NULL is accepted. */
 pb_status pb_graph_free(pb_graph *g);
 

@@ -35,7 +35,9 @@ ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ran
                "pb_count_vertex", "pb_count_edge", "pb_count_all", "pb_wedge_count", "pb_graph_info",
                "pb_graph_free", "pb_kernel_launches", "pb_last_error", "pb_status_string",
                "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc",
-               "pb_set_retrieval", "pb_count_owner_range", "pb_wedge_prefix", "pb_sparsify"]
+               "pb_set_retrieval", "pb_count_owner_range", "pb_wedge_prefix", "pb_sparsify", "pb_autotune",
+               "pb_batch_create", "pb_batch_run", "pb_batch_globals", "pb_batch_vertex", "pb_batch_wedges",
+               "pb_batch_free"]
 
 PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
@@ -54,6 +56,12 @@ class GraphInfo(ctypes.Structure):
                 ("m", ctypes.c_uint64), ("max_deg_U", ctypes.c_uint32), ("max_deg_V", ctypes.c_uint32),
                 ("rank_kind", ctypes.c_int32), ("W", ctypes.c_uint64), ("max_wedges_x1", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("rank_kind", ctypes.c_int32), ("retrieval", ctypes.c_int32), ("agg", ctypes.c_int32),
+                ("hub_cluster", ctypes.c_uint32), ("hub_min", ctypes.c_uint64), ("f_side", ctypes.c_double),
+                ("W_side", ctypes.c_uint64), ("W_rank", ctypes.c_uint64), ("max_owner_wedges", ctypes.c_uint64)]
 
 
 class Profile(ctypes.Structure):
@@ -113,6 +121,16 @@ def load_library(path: str = LIB_PATH):
         lib.pb_wedge_prefix.restype = i32
         lib.pb_sparsify.argtypes = [u32, u32, u64, vp, vp, i32, i32, ctypes.c_double, u64, vp, vp, u64p, vp]
         lib.pb_sparsify.restype = i32
+        lib.pb_autotune.argtypes = [vp, ctypes.POINTER(Plan)]
+        lib.pb_batch_create.argtypes = [ctypes.POINTER(vp), u32, i32, u64, vp, ctypes.POINTER(vp)]
+        lib.pb_batch_run.argtypes = [vp, vp]
+        lib.pb_batch_globals.argtypes = [vp, u64p, vp]
+        lib.pb_batch_vertex.argtypes = [vp, u32, vp, vp, i32, vp]
+        lib.pb_batch_wedges.argtypes = [vp, u64p]
+        lib.pb_batch_free.argtypes = [vp]
+        for f in ("pb_autotune", "pb_batch_create", "pb_batch_run", "pb_batch_globals", "pb_batch_vertex",
+                  "pb_batch_wedges", "pb_batch_free"):
+            getattr(lib, f).restype = i32
         _lib = lib
         return lib
 
@@ -279,6 +297,16 @@ class Graph:
         _check(load_library().pb_set_retrieval(self._h, RETRIEVALS[which]))
         return self
 
+    def autotune(self) -> dict:
+        """The autotuner's plan for this graph (see pb_autotune)."""
+        p = Plan()
+        _check(load_library().pb_autotune(self._h, ctypes.byref(p)))
+        inv_rank = {v: k for k, v in RANKS.items()}
+        inv_rt = {v: k for k, v in RETRIEVALS.items()}
+        return dict(rank=inv_rank.get(p.rank_kind), retrieval=inv_rt.get(p.retrieval), hub_cluster=p.hub_cluster,
+                    hub_min=p.hub_min, f_side=p.f_side, W_side=p.W_side, W_rank=p.W_rank,
+                    max_owner_wedges=p.max_owner_wedges)
+
     def ranks(self, stream=None) -> np.ndarray:
         out = np.empty(self.nU + self.nV, np.uint32)
         _check(load_library().pb_graph_ranks(self._h, ctypes.c_void_p(out.ctypes.data), 0, _stream(stream)))
@@ -358,3 +386,54 @@ class Graph:
                                             ctypes.byref(g) if g is not None else None, ptr(U), ptr(V), ptr(E),
                                             int(on_device), _stream(stream)))
         return Counts(int(g.value) if g is not None else None, U, V, E)
+
+
+class Batch:
+    """Many ranked graphs counted together: one persistent kernel per work
+    tier over all their owners, captured once in a CUDA graph and replayed
+    by run()."""
+
+    def __init__(self, graphs, vertex: bool = True, scratch_bytes: int = 0, stream=None):
+        lib = load_library()
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g._h for g in self.graphs])
+        h = ctypes.c_void_p()
+        _check(lib.pb_batch_create(arr, len(self.graphs), int(vertex), scratch_bytes, _stream(stream),
+                                   ctypes.byref(h)))
+        self._h = h
+        self.vertex = vertex
+
+    def run(self, stream=None):
+        _check(load_library().pb_batch_run(self._h, _stream(stream)))
+
+    def globals(self, stream=None) -> np.ndarray:
+        out = np.empty(len(self.graphs), np.uint64)
+        _check(load_library().pb_batch_globals(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                               _stream(stream)))
+        return out
+
+    def vertex_counts(self, i: int, stream=None):
+        g = self.graphs[i]
+        U = np.empty(g.nU, np.uint64)
+        V = np.empty(g.nV, np.uint64)
+        _check(load_library().pb_batch_vertex(self._h, i, ctypes.c_void_p(U.ctypes.data),
+                                              ctypes.c_void_p(V.ctypes.data), 0, _stream(stream)))
+        return U, V
+
+    @property
+    def wedges(self) -> int:
+        W = ctypes.c_uint64()
+        _check(load_library().pb_batch_wedges(self._h, ctypes.byref(W)))
+        return int(W.value)
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load_library().pb_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+

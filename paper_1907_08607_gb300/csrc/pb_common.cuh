@@ -48,6 +48,7 @@ struct pb_graph {
   uint64_t maxw = 0;          // max wedges of one lower-ranked endpoint
   uint64_t maxw_rev = 0;      // max wedges of one higher-ranked endpoint
   int retrieval = PB_RETRIEVE_AUTO;
+  uint64_t w_side_U = 0, w_side_V = 0;  // wedges with endpoints in U / in V (side order)
 
   // Aggregation scratch, grown on demand and kept until pb_graph_free.
   void *scratch = nullptr;
@@ -152,6 +153,7 @@ struct CountOut {
 };
 pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut &o,
                     cudaStream_t s);
+void make_plan(const pb_graph *g, pb_plan_t *plan);
 
 // head[i] = 1 where keys[i] starts a run of equal keys (pb_graph.cu).
 __global__ void k_heads(const uint64_t *__restrict__ keys, size_t m, uint32_t *__restrict__ head);

@@ -27,6 +27,9 @@
 #include <cooperative_groups.h>
 
 #include <cstdlib>
+#include <new>
+#include <string>
+#include <vector>
 
 #include "pb_common.cuh"
 
@@ -230,18 +233,28 @@ __device__ __forceinline__ void warp_run_add(unsigned long long *acc, uint32_t k
 // steps of 32 wedges in flight per warp.
 constexpr int LW_BATCH = 4;
 
-template <bool PV, bool PE>
-__global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *__restrict__ list,
-                                                      uint32_t nlist) {
+template <bool PV, bool PE, bool MULTI>
+__global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *__restrict__ list,
+                                                      uint32_t nlist, const uint64_t *__restrict__ items,
+                                                      const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP / 2 count words
   __shared__ unsigned long long s_sum[LW_WARPS][32];
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t *key = dsm + w * (LW_CAP + LW_CAP / 2), *cnt = key + LW_CAP;
-  unsigned long long *err = &a.acc[ACC_ERR];
+  unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[w][lane] = 0;
   for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
-    const uint32_t x1 = list[it];
+    uint32_t x1;
+    CArgs a;  // this item's graph
+    if (MULTI) {
+      const uint64_t item = items[it];
+      a = tab[item >> 32];
+      x1 = static_cast<uint32_t>(item);
+    } else {
+      a = a0;
+      x1 = list[it];
+    }
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
@@ -281,7 +294,8 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
     }
     own = warp_sum(own);
     if (lane == 0) {
-      gacc += own;
+      if (MULTI) add_global(a.acc, own);
+      else gacc += own;
       if (PV && own) atomicAdd(&a.pv[x1], own);
     }
     if (PV || PE) {
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a, const uint32_t *_
     }
     __syncwarp();
   }
-  if (lane == 0) add_global(a.acc, gacc);
+  if (!MULTI && lane == 0) add_global(a0.acc, gacc);
 }
 
 // ---------------------------------------------------------------------------
@@ -339,9 +353,10 @@ __device__ __forceinline__ uint32_t block_find(const uint32_t *s_incl, uint32_t 
 }
 
 // Medium tier: one block per first endpoint, table in (dynamic) shared memory.
-template <bool PV, bool PE>
-__global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *__restrict__ list,
-                                                       uint32_t nlist) {
+template <bool PV, bool PE, bool MULTI>
+__global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t *__restrict__ list,
+                                                       uint32_t nlist, const uint64_t *__restrict__ items,
+                                                       const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t dsm[];
   uint32_t *key = dsm, *cnt = dsm + MB_CAP;
   __shared__ uint32_t s_incl[MB_THREADS], s_ex[MB_THREADS], s_oy[MB_THREADS];
@@ -353,11 +368,20 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   for (;;) {
-    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QMED], 1ull));
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= nlist) break;
-    const uint32_t x1 = list[it];
+    uint32_t x1;
+    CArgs a;  // this item's graph
+    if (MULTI) {
+      const uint64_t item = items[it];
+      a = tab[item >> 32];
+      x1 = static_cast<uint32_t>(item);
+    } else {
+      a = a0;
+      x1 = list[it];
+    }
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
@@ -392,7 +416,8 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
     }
     own = block_sum(own, s_w64);
     if (tid == 0) {
-      gacc += own;
+      if (MULTI) add_global(a.acc, own);
+      else gacc += own;
       if (PV && own) atomicAdd(&a.pv[x1], own);
     }
     if (PV || PE) {
@@ -436,7 +461,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a, const uint32_t *
     }
     __syncthreads();
   }
-  if (tid == 0) add_global(a.acc, gacc);
+  if (!MULTI && tid == 0) add_global(a0.acc, gacc);
 }
 
 // ---------------------------------------------------------------------------
@@ -527,9 +552,10 @@ __device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot
   return __ldcg(&val[p]);
 }
 
-template <bool PV, bool PE, bool DENSE>
-__global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *__restrict__ list,
-                                                      uint32_t nlist, HeavySlots h) {
+template <bool PV, bool PE, bool DENSE, bool MULTI>
+__global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *__restrict__ list,
+                                                      uint32_t nlist, HeavySlots h, const uint64_t *__restrict__ items,
+                                                      const CArgs *__restrict__ tab) {
   cg::cluster_group cl = cg::this_cluster();
   const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
   const uint32_t slot = blockIdx.x / csize;
@@ -540,17 +566,26 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
   __shared__ unsigned long long s_w64[33];
   uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.side : nullptr;
   uint32_t *T = DENSE ? h.T + static_cast<size_t>(slot) * h.tcap : nullptr;
-  unsigned long long *err = &a.acc[ACC_ERR];
+  unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   for (uint32_t k = 0;; k++) {
-    if (crank == 0 && tid == 0) h.item[slot] = static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QHEAVY], 1ull));
+    if (crank == 0 && tid == 0) h.item[slot] = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QHEAVY], 1ull));
     cl.sync();
     const uint32_t it = __ldcg(&h.item[slot]);
     if (it >= nlist) break;
     uint32_t *tc = &h.tcnt[2 * slot + (k & 1)];
     if (crank == 0 && tid == 0) h.tcnt[2 * slot + ((k + 1) & 1)] = 0;
-    const uint32_t x1 = list[it];
+    uint32_t x1;
+    CArgs a;  // this item's graph
+    if (MULTI) {
+      const uint64_t item = items[it];
+      a = tab[item >> 32];
+      x1 = static_cast<uint32_t>(item);
+    } else {
+      a = a0;
+      x1 = list[it];
+    }
     const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     const int lg = DENSE ? 0 : table_lg(wc, a.n, a.nU, x1, a.rev);
@@ -624,7 +659,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
     }
     own = block_sum(own, s_w64);
     if (tid == 0) {
-      gacc += own;
+      if (MULTI) add_global(a.acc, own);
+      else gacc += own;
       if (PV && own) atomicAdd(&a.pv[x1], own);
     }
     // ---- centres and edges
@@ -693,7 +729,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a, const uint32_t *_
       }
     }
   }
-  if (tid == 0) add_global(a.acc, gacc);
+  if (!MULTI && tid == 0) add_global(a0.acc, gacc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,22 +1049,24 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
     if (nl) {
       PhaseScope ph(PB_PHASE_LIGHT, s);
       const size_t smem = LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t);
-      PB_CUDA(cudaFuncSetAttribute(k_light<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PB_CUDA(cudaFuncSetAttribute(k_light<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_light<PV, PE>, LW_THREADS, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_light<PV, PE, false>, LW_THREADS, smem);
       unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
       unsigned need = (nl + LW_WARPS - 1) / LW_WARPS;
-      PB_LAUNCH((k_light<PV, PE>), grid < need ? grid : need, LW_THREADS, smem, s, a, light, nl);
+      PB_LAUNCH((k_light<PV, PE, false>), grid < need ? grid : need, LW_THREADS, smem, s, a, light, nl,
+                (const uint64_t *)nullptr, (const CArgs *)nullptr);
       ph.finish(s, hcnt[ACC_WLIGHT]);
     }
     if (nm) {
       PhaseScope ph(PB_PHASE_MEDIUM, s);
       const size_t smem = 2 * MB_CAP * sizeof(uint32_t);
-      PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE>, MB_THREADS, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE, false>, MB_THREADS, smem);
       unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
-      PB_LAUNCH((k_medium<PV, PE>), grid < nm ? grid : nm, MB_THREADS, smem, s, a, med, nm);
+      PB_LAUNCH((k_medium<PV, PE, false>), grid < nm ? grid : nm, MB_THREADS, smem, s, a, med, nm,
+                (const uint64_t *)nullptr, (const CArgs *)nullptr);
       ph.finish(s, hcnt[ACC_WMED]);
     }
     if (nh) {
@@ -1055,14 +1093,29 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         hs.hcap = cap;
         slot_bytes = 2 * cap * sizeof(uint32_t);
       }
-      auto kern = p.dense ? k_heavy<PV, PE, true> : k_heavy<PV, PE, false>;
+      auto kern = p.dense ? k_heavy<PV, PE, true, false> : k_heavy<PV, PE, false, false>;
       // Hubs (wedges > hub_min, the head of the largest-first list) get one
       // cluster each; the rest one block each (plain batching).
-      const uint32_t nhub = p.cluster > 1 ? static_cast<uint32_t>(hcnt[ACC_NHUB]) : 0;
-      struct Part { const uint32_t *list; uint32_t cnt; unsigned cl; };
-      Part parts[2] = {{heavy, nhub, p.cluster}, {heavy + nhub, nh - nhub, 1}};
+      uint32_t nhub = p.cluster > 1 ? static_cast<uint32_t>(hcnt[ACC_NHUB]) : 0;
+      unsigned hub_cl = p.cluster, rest_cl = 1;
       uint64_t fit = budget / (slot_bytes + 16);
       if (fit == 0) { st = fail(PB_ERR_SCRATCH, "scratch budget %llu B below one heavy slot (%llu B)", (unsigned long long)budget, (unsigned long long)slot_bytes); break; }
+      {
+        // When the budget holds fewer slots than there are resident blocks,
+        // every slot is shared by a cluster of blocks so that all SMs work.
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy<PV, PE, true, false>, HB_THREADS, 0);
+        const uint64_t resident = static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1);
+        if (fit < resident) {
+          uint64_t want = (resident + fit - 1) / fit;
+          unsigned c = 1;
+          while (c < want && c < 8) c <<= 1;
+          rest_cl = c;
+          if (hub_cl < c) hub_cl = c;
+        }
+      }
+      struct Part { const uint32_t *list; uint32_t cnt; unsigned cl; };
+      Part parts[2] = {{heavy, nhub, hub_cl}, {heavy + nhub, nh - nhub, rest_cl}};
       PhaseScope ph(PB_PHASE_HEAVY, s);
       for (const Part &pt : parts) {
         if (pt.cnt == 0) continue;
@@ -1071,7 +1124,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         int nc = max_clusters(kern, HB_THREADS, cl);
         if (nc <= 0) nc = sms / static_cast<int>(cl);
         uint64_t nslots = static_cast<uint64_t>(nc);
-        if (cl > 1 && p.max_slots && nslots > p.max_slots) nslots = p.max_slots;
+        if (&pt == &parts[0] && p.max_slots && nslots > p.max_slots) nslots = p.max_slots;
         if (nslots > fit) nslots = fit;
         if (nslots > pt.cnt) nslots = pt.cnt;
         size_t need = nslots * slot_bytes + nslots * 3 * sizeof(uint32_t) + 64;
@@ -1093,7 +1146,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, s, a, pt.list, pt.cnt,
-                                 hs)) != PB_OK) break;
+                                 hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) break;
       }
       if (st != PB_OK) break;
       ph.finish(s, hcnt[ACC_WHEAVY]);
@@ -1200,7 +1253,9 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
   CArgs a;
   // Owner of each wedge: its lower-ranked endpoint (Algorithm 2) or, with the
   // cache optimisation, its higher-ranked one.  Same wedges either way.
-  a.rev = g->retrieval == PB_RETRIEVE_LOW ? 0 : 1;
+  pb_plan_t plan;
+  make_plan(g, &plan);
+  a.rev = g->retrieval == PB_RETRIEVE_AUTO ? plan.retrieval == PB_RETRIEVE_HIGH : g->retrieval == PB_RETRIEVE_HIGH;
   a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.n = n;
   a.wpre = a.rev ? g->wpre_rev : g->wpre;
   a.nU = g->nU;
@@ -1217,9 +1272,9 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     p.owner_lo = o.owner_lo < n ? o.owner_lo : n;
     p.owner_hi = o.owner_hi < n ? o.owner_hi : n;
     p.dense = agg != PB_AGG_HASH;
-    p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", 2));
+    p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", plan.hub_cluster));
     p.max_slots = env_u64("PB_HEAVY_SLOTS", 0);
-    p.hub_min = env_u64("PB_HUB_MIN", uint64_t(1) << 18);
+    p.hub_min = env_u64("PB_HUB_MIN", plan.hub_min);
     if (agg == PB_AGG_BATCH) {
       p.med_max = LIGHT_MAX;  // everything above the light tier uses dense arrays
       p.cluster = 1;
@@ -1285,3 +1340,368 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
 }
 
 }  // namespace pb
+
+namespace pb {
+
+// ---------------------------------------------------------------------------
+// Autotuner (rules from degree and wedge statistics).
+void make_plan(const pb_graph *g, pb_plan_t *plan) {
+  const uint64_t w_side = g->w_side_U < g->w_side_V ? g->w_side_U : g->w_side_V;
+  plan->W_side = w_side;
+  plan->W_rank = g->W;
+  plan->f_side = w_side ? (static_cast<double>(w_side) - static_cast<double>(g->W)) / static_cast<double>(w_side) : 0.0;
+  // side order when the ranking saves under 10% of its wedges (Table 3's rule)
+  plan->rank_kind = plan->f_side < 0.1 ? PB_RANK_SIDE : (g->rank_kind >= 0 && g->rank_kind <= 2 ? g->rank_kind
+                                                                                                   : PB_RANK_DEGREE);
+  const bool high = g->maxw_rev <= g->maxw;
+  plan->retrieval = high ? PB_RETRIEVE_HIGH : PB_RETRIEVE_LOW;
+  plan->max_owner_wedges = high ? g->maxw_rev : g->maxw;
+  plan->agg = PB_AGG_AUTO;
+  // owners past 2^20 wedges would keep one block busy for milliseconds:
+  // give owners past 2^18 a pair of blocks
+  if (plan->max_owner_wedges > (uint64_t(1) << 20)) {
+    plan->hub_min = uint64_t(1) << 18;
+    plan->hub_cluster = 2;
+  } else {
+    plan->hub_min = UINT64_MAX;
+    plan->hub_cluster = 1;
+  }
+}
+
+}  // namespace pb
+
+// ---------------------------------------------------------------------------
+// Batched counting across graphs.
+struct pb_batch {
+  int device = 0;
+  uint32_t ng = 0;
+  bool pv = false;
+  std::vector<pb_graph *> graphs;
+  std::vector<uint64_t> pv_off;          // start of each graph's counts in pvbuf
+  pb::CArgs *tab = nullptr;               // [ng] device
+  unsigned long long *acc = nullptr;      // [ng][ACC_WORDS] per-graph accumulators
+  unsigned long long *bacc = nullptr;     // [ACC_WORDS] batch work queues
+  unsigned long long *pvbuf = nullptr;    // per-vertex counts, all graphs
+  uint64_t pv_total = 0;
+  uint64_t *light = nullptr, *med = nullptr, *heavy = nullptr;
+  uint32_t nl = 0, nm = 0, nh = 0;
+  pb::HeavySlots hs = {};
+  void *scratch = nullptr;
+  uint64_t nslots = 0, slot_bytes = 0;
+  uint64_t W = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace pb {
+
+__global__ void k_tag_items(const uint32_t *__restrict__ list, uint32_t cnt, uint32_t gid,
+                            uint64_t *__restrict__ out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    out[i] = (static_cast<uint64_t>(gid) << 32) | list[i];
+}
+
+static void batch_release(pb_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaStream_t s = 0;
+  dfree(b->tab, s); dfree(b->acc, s); dfree(b->bacc, s); dfree(b->pvbuf, s);
+  dfree(b->light, s); dfree(b->med, s); dfree(b->heavy, s); dfree(b->scratch, s);
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  delete b;
+}
+
+template <bool PV>
+static pb_status batch_capture_on(pb_batch *b, cudaStream_t s);
+
+// The launches are recorded on a private stream (the legacy default stream
+// cannot be captured); the resulting graph is launched on any stream.
+template <bool PV>
+static pb_status batch_capture(pb_batch *b) {
+  cudaStream_t cs = nullptr;
+  PB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  pb_status st = batch_capture_on<PV>(b, cs);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
+template <bool PV>
+static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
+  const int sms = sm_count(b->device);
+  CArgs a0 = {};
+  a0.acc = b->bacc;
+  PB_CUDA(cudaFuncSetAttribute(k_light<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t))));
+  PB_CUDA(cudaFuncSetAttribute(k_medium<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(2 * MB_CAP * sizeof(uint32_t))));
+  PB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  pb_status st = PB_OK;
+  do {
+    cudaError_t e1 = cudaMemsetAsync(b->acc, 0, sizeof(unsigned long long) * ACC_WORDS * b->ng, s);
+    if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (accumulators)", __FILE__, __LINE__); break; }
+    e1 = cudaMemsetAsync(b->bacc, 0, sizeof(unsigned long long) * ACC_WORDS, s);
+    if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (queues)", __FILE__, __LINE__); break; }
+    if (PV) {
+      e1 = cudaMemsetAsync(b->pvbuf, 0, sizeof(unsigned long long) * (b->pv_total + 1), s);
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (per-vertex)", __FILE__, __LINE__); break; }
+    }
+    if (b->nl) {
+      const size_t smem = LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t);
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_light<PV, false, true>, LW_THREADS, smem);
+      unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
+      unsigned need = (b->nl + LW_WARPS - 1) / LW_WARPS;
+      k_light<PV, false, true><<<grid < need ? grid : need, LW_THREADS, smem, s>>>(a0, nullptr, b->nl, b->light, b->tab);
+      count_launch();
+      e1 = cudaGetLastError();
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch light launch", __FILE__, __LINE__); break; }
+    }
+    if (b->nm) {
+      const size_t smem = 2 * MB_CAP * sizeof(uint32_t);
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, false, true>, MB_THREADS, smem);
+      unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
+      k_medium<PV, false, true><<<grid < b->nm ? grid : b->nm, MB_THREADS, smem, s>>>(a0, nullptr, b->nm, b->med, b->tab);
+      count_launch();
+      e1 = cudaGetLastError();
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch medium launch", __FILE__, __LINE__); break; }
+    }
+    if (b->nh) {
+      e1 = cudaMemsetAsync(b->scratch, 0, b->nslots * b->slot_bytes + b->nslots * 7 * sizeof(uint32_t) + 64, s);
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (slots)", __FILE__, __LINE__); break; }
+      if ((st = launch_cluster(k_heavy<PV, false, true, true>, static_cast<unsigned>(b->nslots), HB_THREADS, 1, s, a0,
+                               (const uint32_t *)nullptr, b->nh, b->hs, (const uint64_t *)b->heavy,
+                               (const CArgs *)b->tab)) != PB_OK) break;
+    }
+  } while (0);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st != PB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch capture", __FILE__, __LINE__);
+  b->graph = graph;
+  PB_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+  return PB_OK;
+}
+
+static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
+  const uint32_t ng = b->ng;
+  // per-graph argument table and output buffers
+  std::vector<CArgs> host_tab(ng);
+  b->pv_off.resize(ng);
+  uint64_t total_n = 0, max_side = 1;
+  for (uint32_t i = 0; i < ng; i++) {
+    pb_graph *g = b->graphs[i];
+    b->pv_off[i] = total_n;
+    total_n += g->n;
+    uint64_t side = g->nU > g->nV ? g->nU : g->nV;
+    if (side > max_side) max_side = side;
+  }
+  b->pv_total = total_n;
+  PB_TRY(dalloc_t(&b->acc, static_cast<size_t>(ng) * ACC_WORDS, s));
+  PB_TRY(dalloc_t(&b->bacc, ACC_WORDS, s));
+  PB_TRY(dalloc_t(&b->pvbuf, total_n + 1, s));
+  PB_TRY(dalloc_t(&b->light, total_n + 1, s));
+  PB_TRY(dalloc_t(&b->med, total_n + 1, s));
+  PB_TRY(dalloc_t(&b->heavy, total_n + 1, s));
+  uint32_t *tl = nullptr, *tm = nullptr;
+  uint64_t *th = nullptr;
+  unsigned long long *tacc = nullptr;
+  pb_status st = PB_OK;
+  uint64_t max_bound = 1;
+  do {
+    if ((st = dalloc_t(&tacc, ACC_WORDS, s)) != PB_OK) break;
+    for (uint32_t i = 0; i < ng && st == PB_OK; i++) {
+      pb_graph *g = b->graphs[i];
+      pb_plan_t plan;
+      make_plan(g, &plan);
+      CArgs &a = host_tab[i];
+      a.rev = g->retrieval == PB_RETRIEVE_AUTO ? plan.retrieval == PB_RETRIEVE_HIGH : g->retrieval == PB_RETRIEVE_HIGH;
+      a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.n = g->n; a.nU = g->nU;
+      a.wpre = a.rev ? g->wpre_rev : g->wpre;
+      a.pv = b->pv ? b->pvbuf + b->pv_off[i] : nullptr;
+      a.es = nullptr;
+      a.acc = b->acc + static_cast<size_t>(i) * ACC_WORDS;
+      b->W += g->W;
+      if (g->W == 0) continue;
+      const uint64_t n = g->n;
+      if ((st = dalloc_t(&tl, n + 1, s)) != PB_OK || (st = dalloc_t(&tm, n + 1, s)) != PB_OK ||
+          (st = dalloc_t(&th, n + 1, s)) != PB_OK) break;
+      if (cudaMemsetAsync(tacc, 0, sizeof(unsigned long long) * ACC_WORDS, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, 0, n, LIGHT_MAX, MED_MAX, UINT64_MAX, tl, tm, th,
+                                                        g->bitsN, tacc);
+      count_launch();
+      unsigned long long hc[ACC_WORDS];
+      if (cudaMemcpyAsync(hc, tacc, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "classify readback"); break; }
+      const uint32_t cl = static_cast<uint32_t>(hc[ACC_NLIGHT]), cm = static_cast<uint32_t>(hc[ACC_NMED]),
+                     ch = static_cast<uint32_t>(hc[ACC_NHEAVY]);
+      if (cl) { k_tag_items<<<grid_for(cl, 256, 1024), 256, 0, s>>>(tl, cl, i, b->light + b->nl); count_launch(); }
+      if (cm) { k_tag_items<<<grid_for(cm, 256, 1024), 256, 0, s>>>(tm, cm, i, b->med + b->nm); count_launch(); }
+      if (ch) {
+        k_keys_low<<<grid_for(ch, 256, 1024), 256, 0, s>>>(th, ch, g->bitsN, tl);
+        count_launch();
+        k_tag_items<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, i, b->heavy + b->nh);
+        count_launch();
+        // distinct bound of this graph's heavy owners
+        if (cudaMemsetAsync(tacc, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        k_max_wedges_list<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, a.wpre, n, g->nU, a.rev, tacc);
+        count_launch();
+        unsigned long long bd = 0;
+        if (cudaMemcpyAsync(&bd, tacc, sizeof(bd), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
+        if (bd > max_bound) max_bound = bd;
+      }
+      b->nl += cl; b->nm += cm; b->nh += ch;
+      dfree(tl, s); dfree(tm, s); dfree(th, s);
+      tl = tm = nullptr; th = nullptr;
+    }
+  } while (0);
+  dfree(tl, s); dfree(tm, s); dfree(th, s); dfree(tacc, s);
+  if (st != PB_OK) return st;
+  PB_TRY(dalloc_t(&b->tab, ng, s));
+  PB_CUDA(cudaMemcpyAsync(b->tab, host_tab.data(), sizeof(CArgs) * ng, cudaMemcpyHostToDevice, s));
+  if (b->nh) {
+    b->hs.side = max_side;
+    b->hs.tcap = max_bound < max_side ? max_bound : max_side;
+    b->slot_bytes = (b->hs.side + b->hs.tcap) * sizeof(uint32_t);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy<true, false, true, true>, HB_THREADS, 0);
+    uint64_t ns = static_cast<uint64_t>(sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
+    uint64_t fit = budget / (b->slot_bytes + 32);
+    if (fit == 0) return fail(PB_ERR_SCRATCH, "batch scratch budget below one slot");
+    if (ns > fit) ns = fit;
+    if (ns > b->nh) ns = b->nh;
+    b->nslots = ns;
+    PB_TRY(dalloc(&b->scratch, ns * b->slot_bytes + ns * 7 * sizeof(uint32_t) + 64, s));
+    char *sp = static_cast<char *>(b->scratch);
+    b->hs.A = reinterpret_cast<uint32_t *>(sp);
+    b->hs.T = b->hs.A + ns * b->hs.side;
+    b->hs.tcnt = b->hs.T + ns * b->hs.tcap;
+    b->hs.item = b->hs.tcnt + 2 * ns;
+  }
+  PB_CUDA(cudaStreamSynchronize(s));
+  return b->pv ? batch_capture<true>(b) : batch_capture<false>(b);
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" {
+
+pb_status pb_autotune(const pb_graph *g, pb_plan_t *plan) {
+  clear_error();
+  if (!g || !plan) return fail(PB_ERR_INVALID, "graph or plan is NULL");
+  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
+  make_plan(g, plan);
+  return PB_OK;
+}
+
+pb_status pb_batch_create(pb_graph *const *graphs, uint32_t ng, int want_vertex, uint64_t scratch_bytes,
+                          void *stream, pb_batch **out) {
+  clear_error();
+  if (!out || (ng && !graphs)) return fail(PB_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  pb_batch *b = new (std::nothrow) pb_batch();
+  if (!b) return fail(PB_ERR_NOMEM, "host allocation failed");
+  cudaGetDevice(&b->device);
+  b->ng = ng;
+  b->pv = want_vertex != 0;
+  for (uint32_t i = 0; i < ng; i++) {
+    if (!graphs[i] || graphs[i]->rank_kind < 0 || graphs[i]->device != b->device) {
+      delete b;
+      return fail(PB_ERR_INVALID, "graph %u is NULL, not ranked, or on another device", i);
+    }
+    if (graphs[i]->n >= (uint64_t(1) << 32)) { delete b; return fail(PB_ERR_INVALID, "graph too large"); }
+    b->graphs.push_back(graphs[i]);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pb_status st = batch_build(b, scratch_bytes ? scratch_bytes : (uint64_t(16) << 30), s);
+  if (st != PB_OK) {
+    std::string keep = pb_last_error();
+    batch_release(b);
+    fail(st, "%s", keep.c_str());
+    return st;
+  }
+  *out = b;
+  return PB_OK;
+}
+
+pb_status pb_batch_run(pb_batch *b, void *stream) {
+  clear_error();
+  if (!b) return fail(PB_ERR_INVALID, "batch is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PhaseScope ph(PB_PHASE_HEAVY, s);
+  PB_CUDA(cudaGraphLaunch(b->exec, s));
+  count_launch((b->nl ? 1 : 0) + (b->nm ? 1 : 0) + (b->nh ? 1 : 0));
+  ph.finish(s, b->W);
+  PB_CUDA(cudaStreamSynchronize(s));
+  prof_flush();
+  return PB_OK;
+}
+
+pb_status pb_batch_globals(const pb_batch *b, uint64_t *out, void *stream) {
+  clear_error();
+  if (!b || !out) return fail(PB_ERR_INVALID, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<unsigned long long> h(static_cast<size_t>(b->ng) * ACC_WORDS);
+  if (b->ng) {
+    PB_CUDA(cudaMemcpyAsync(h.data(), b->acc, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PB_CUDA(cudaStreamSynchronize(s));
+  }
+  for (uint32_t i = 0; i < b->ng; i++) {
+    const unsigned long long *r = &h[static_cast<size_t>(i) * ACC_WORDS];
+    if (r[ACC_ERR]) return fail(PB_ERR_SCRATCH, "graph %u: aggregation table overflow", i);
+    if (r[ACC_OVF]) return fail(PB_ERR_OVERFLOW, "graph %u: global count exceeds 2^64", i);
+    out[i] = r[ACC_GLOBAL];
+  }
+  return PB_OK;
+}
+
+pb_status pb_batch_vertex(const pb_batch *b, uint32_t i, uint64_t *out_U, uint64_t *out_V, int out_on_device,
+                          void *stream) {
+  clear_error();
+  if (!b || i >= b->ng || !b->pv) return fail(PB_ERR_INVALID, "bad batch, index or no per-vertex counts");
+  const pb_graph *g = b->graphs[i];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint64_t *dU = out_U, *dV = out_V, *tmp = nullptr;
+  if (!out_on_device) {
+    PB_TRY(dalloc_t(&tmp, g->n + 1, s));
+    dU = out_U ? tmp : nullptr;
+    dV = out_V ? tmp + g->nU : nullptr;
+  }
+  k_out_vertex<<<grid_for(g->n, 256, 8192), 256, 0, s>>>(b->pvbuf + b->pv_off[i], g->label, g->nU, g->nV, dU, dV);
+  count_launch();
+  pb_status st = PB_OK;
+  if (!out_on_device) {
+    if ((out_U && cudaMemcpyAsync(out_U, dU, g->nU * 8ull, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        (out_V && cudaMemcpyAsync(out_V, dV, g->nV * 8ull, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+      st = fail(PB_ERR_CUDA, "download");
+  }
+  dfree(tmp, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st != PB_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "batch vertex output", __FILE__, __LINE__);
+  return PB_OK;
+}
+
+pb_status pb_batch_wedges(const pb_batch *b, uint64_t *W) {
+  clear_error();
+  if (!b || !W) return fail(PB_ERR_INVALID, "NULL argument");
+  *W = b->W;
+  return PB_OK;
+}
+
+pb_status pb_batch_free(pb_batch *b) {
+  clear_error();
+  batch_release(b);
+  return PB_OK;
+}
+
+}  // extern "C"
+

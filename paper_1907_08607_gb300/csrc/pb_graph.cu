@@ -400,6 +400,16 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
   do {
     if ((st = dalloc_t(&acc, 2, s)) != PB_OK) break;
     if (cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    // ---- 0. wedges of side order (input to the ranking choice)
+    if (n) {
+      k_side_wedges<<<grid_for(n, 256, 2048), 256, 0, s>>>(g->deg, n, g->nU, acc);
+      count_launch();
+    }
+    if (cudaMemcpyAsync(hacc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "side wedge readback"); break; }
+    g->w_side_U = hacc[0];
+    g->w_side_V = hacc[1];
+    if (cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
     // ---- 1. the ranking
     if (rank_of) {
       const uint32_t *src = rank_of;
@@ -420,13 +430,7 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       dfree(tmp, s);
       tmp = nullptr;
     } else if (kind == PB_RANK_SIDE) {
-      if (n) {
-        k_side_wedges<<<grid_for(n, 256, 2048), 256, 0, s>>>(g->deg, n, g->nU, acc);
-        count_launch();
-      }
-      if (cudaMemcpyAsync(hacc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "side wedge readback"); break; }
-      int u_first = hacc[0] <= hacc[1];
+      int u_first = g->w_side_U <= g->w_side_V;
       if (n) {
         k_side_rank<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, g->nU, g->nV, u_first, g->rank, g->order);
         count_launch();
