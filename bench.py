@@ -145,6 +145,23 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def measured_traffic(kernel: str, wedges_per_launch: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture,
+    scaled by wedges; None when the capture is of another kernel or the
+    kernel source has changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, t["source_file"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if t.get("kernel") != kernel or sha != t.get("source_sha256"):
+        return None
+    return t["dram_bytes_per_wedge"] * wedges_per_launch
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -322,7 +339,8 @@ def run_gb300(args):
         per_launch_bytes = BYTES_PER_WEDGE[args.outputs] * kp["wedges"] / kp["records"]
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": kern, "peak_source": peak_src,
+                "traffic": measured_traffic(kern, kp["wedges"] / kp["records"]), "kernel": kern,
+                "peak_source": peak_src,
                 "launch_ms": per_launch_ms, "algorithmic_bytes_per_launch": per_launch_bytes}
 
     if rank != 0:
@@ -345,6 +363,7 @@ def run_gb300(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["records"]},
+        "phases_wedges_per_step": {k: v["wedges"] // args.steps for k, v in prof.items() if v["wedges"]},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
