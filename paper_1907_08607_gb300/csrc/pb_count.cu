@@ -59,7 +59,7 @@ enum { ACC_GLOBAL = 0, ACC_OVF = 1, ACC_QMED = 2, ACC_QHEAVY = 3, ACC_NLIGHT = 4
 // load <= 1/2 unless scratch is corrupt) records an error instead of spinning.
 
 constexpr uint32_t LIGHT_MAX = 512;   // wedges of a light first endpoint
-constexpr int LW_THREADS = 256;
+constexpr int LW_THREADS = 512;
 constexpr int LW_WARPS = LW_THREADS / 32;
 constexpr int LW_CAP = 1024;          // per-warp table entries (>= 2 * LIGHT_MAX)
 constexpr uint32_t MED_MAX = 4096;
@@ -71,6 +71,39 @@ __device__ __forceinline__ void add_global(unsigned long long *acc, unsigned lon
   if (!v) return;
   unsigned long long old = atomicAdd(&acc[ACC_GLOBAL], v);
   if (old + v < old) atomicAdd(&acc[ACC_OVF], 1ull);
+}
+
+// Per-vertex counts of the lowest labels of each side (the highest-degree
+// vertices under degree-like rankings) are hit by many owners at once when
+// owners are the higher-ranked endpoints.  Blocks add them into a shared
+// array first and flush it once at the end.
+constexpr int HUBK = 512;  // cached labels per side
+
+__device__ __forceinline__ void pv_add(unsigned long long *s_hub, const CArgs &a, uint32_t x,
+                                       unsigned long long b) {
+  if (s_hub) {
+    const uint32_t side = x < a.nU ? 0u : 1u;
+    const uint32_t o = x - (side ? a.nU : 0u);
+    if (o < HUBK) {
+      atomicAdd(&s_hub[side * HUBK + o], b);
+      return;
+    }
+  }
+  atomicAdd(&a.pv[x], b);
+}
+
+__device__ __forceinline__ void hub_zero(unsigned long long *s_hub) {
+  for (uint32_t t = threadIdx.x; t < 2 * HUBK; t += blockDim.x) s_hub[t] = 0;
+}
+
+// Called by the whole block after its last owner.
+__device__ __forceinline__ void hub_flush(unsigned long long *s_hub, const CArgs &a) {
+  for (uint32_t t = threadIdx.x; t < 2 * HUBK; t += blockDim.x) {
+    unsigned long long v = s_hub[t];
+    if (!v) continue;
+    const uint64_t x = t < HUBK ? t : static_cast<uint64_t>(a.nU) + (t - HUBK);
+    if (x < a.n) atomicAdd(&a.pv[x], v);
+  }
 }
 
 __device__ __forceinline__ uint32_t hash_home(uint32_t x, int lg) {
@@ -239,11 +272,15 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *
                                                       const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP / 2 count words
   __shared__ unsigned long long s_sum[LW_WARPS][32];
+  __shared__ unsigned long long s_hubarr[2 * HUBK];
+  unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t *key = dsm + w * (LW_CAP + LW_CAP / 2), *cnt = key + LW_CAP;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[w][lane] = 0;
+  if (s_hub) hub_zero(s_hub);
+  __syncthreads();
   for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
     uint32_t x1;
     CArgs a;  // this item's graph
@@ -289,7 +326,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *
       if (k != EMPTY) {
         unsigned long long d = cnt16_at(cnt, t), b = d * (d - 1) / 2;
         own += b;
-        if (PV && b) atomicAdd(&a.pv[k], b);
+        if (PV && b) pv_add(s_hub, a, k, b);
       }
     }
     own = warp_sum(own);
@@ -327,7 +364,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *
         if (v) {
           unsigned long long sm = s_sum[w][lane];
           if (sm) {
-            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PV) pv_add(s_hub, a, y, sm);
             if (PE) atomicAdd(&a.es[base + i], sm);
             s_sum[w][lane] = 0;
           }
@@ -338,6 +375,8 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *
     __syncwarp();
   }
   if (!MULTI && lane == 0) add_global(a0.acc, gacc);
+  __syncthreads();
+  if (s_hub) hub_flush(s_hub, a0);
 }
 
 // ---------------------------------------------------------------------------
@@ -357,8 +396,10 @@ template <bool PV, bool PE, bool MULTI>
 __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t *__restrict__ list,
                                                        uint32_t nlist, const uint64_t *__restrict__ items,
                                                        const CArgs *__restrict__ tab) {
-  extern __shared__ uint32_t dsm[];
+  extern __shared__ uint32_t dsm[];  // MB_CAP keys, then MB_CAP / 2 words of 16-bit counts
   uint32_t *key = dsm, *cnt = dsm + MB_CAP;
+  __shared__ unsigned long long s_hubarr[2 * HUBK];
+  unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   __shared__ uint32_t s_incl[MB_THREADS], s_ex[MB_THREADS], s_oy[MB_THREADS];
   __shared__ unsigned long long s_sum[MB_THREADS];
   __shared__ uint32_t s_w[33];
@@ -367,6 +408,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
   const uint32_t tid = threadIdx.x;
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
+  if (s_hub) hub_zero(s_hub);
   for (;;) {
     if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
     __syncthreads();
@@ -385,7 +427,8 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
-    for (uint32_t t = tid; t < cap; t += MB_THREADS) { key[t] = EMPTY; cnt[t] = 0; }
+    for (uint32_t t = tid; t < cap; t += MB_THREADS) key[t] = EMPTY;
+    for (uint32_t t = tid; t < cap / 2; t += MB_THREADS) cnt[t] = 0;
     __syncthreads();
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
@@ -401,7 +444,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
       __syncthreads();
       for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
         uint32_t src = block_find(s_incl, MB_THREADS, wi);
-        sh_add(key, cnt, lg, a.adj[s_oy[src] + (wi - s_ex[src])], &a.acc[ACC_ERR]);
+        sh_add16(key, cnt, lg, a.adj[s_oy[src] + (wi - s_ex[src])], &a.acc[ACC_ERR]);
       }
       __syncthreads();
     }
@@ -409,9 +452,9 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
     for (uint32_t t = tid; t < cap; t += MB_THREADS) {
       uint32_t k = key[t];
       if (k != EMPTY) {
-        unsigned long long d = cnt[t], b = d * (d - 1) / 2;
+        unsigned long long d = cnt16_at(cnt, t), b = d * (d - 1) / 2;
         own += b;
-        if (PV && b) atomicAdd(&a.pv[k], b);
+        if (PV && b) pv_add(s_hub, a, k, b);
       }
     }
     own = block_sum(own, s_w64);
@@ -439,7 +482,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
           if (wi < tot) {
             src = block_find(s_incl, MB_THREADS, wi);
             uint32_t slot = s_oy[src] + (wi - s_ex[src]);
-            uint32_t d = sh_get(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
+            uint32_t d = sh_get16(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
             if (d > 1) {
               t = d - 1;
               if (PE) atomicAdd(&a.es[slot], t);
@@ -451,7 +494,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
         if (v) {
           unsigned long long sm = s_sum[tid];
           if (sm) {
-            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PV) pv_add(s_hub, a, y, sm);
             if (PE) atomicAdd(&a.es[base + i], sm);
             s_sum[tid] = 0;
           }
@@ -462,6 +505,8 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
     __syncthreads();
   }
   if (!MULTI && tid == 0) add_global(a0.acc, gacc);
+  __syncthreads();
+  if (s_hub) hub_flush(s_hub, a0);
 }
 
 // ---------------------------------------------------------------------------
@@ -564,11 +609,14 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
   __shared__ unsigned long long s_sum[HB_THREADS];
   __shared__ uint32_t s_w[33];
   __shared__ unsigned long long s_w64[33];
+  __shared__ unsigned long long s_hubarr[2 * HUBK];
+  unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.side : nullptr;
   uint32_t *T = DENSE ? h.T + static_cast<size_t>(slot) * h.tcap : nullptr;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
+  if (s_hub) hub_zero(s_hub);
   for (uint32_t k = 0;; k++) {
     if (crank == 0 && tid == 0) h.item[slot] = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QHEAVY], 1ull));
     cl.sync();
@@ -642,7 +690,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
         uint32_t x2 = __ldcg(&T[t]);
         unsigned long long d = __ldcg(&A[x2 - base]), b = d * (d - 1) / 2;
         own += b;
-        if (PV && b) atomicAdd(&a.pv[x2], b);
+        if (PV && b) pv_add(s_hub, a, x2, b);
       }
     } else {
       const uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
@@ -653,7 +701,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
         if (kk != EMPTY) {
           unsigned long long d = __ldcg(&val[t]), b = d * (d - 1) / 2;
           own += b;
-          if (PV && b) atomicAdd(&a.pv[kk], b);
+          if (PV && b) pv_add(s_hub, a, kk, b);
         }
       }
     }
@@ -706,7 +754,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
         if (v) {
           unsigned long long sm = s_sum[tid];
           if (sm) {
-            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PV) pv_add(s_hub, a, y, sm);
             if (PE) atomicAdd(&a.es[xbase + i], sm);
             s_sum[tid] = 0;
           }
@@ -730,6 +778,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
     }
   }
   if (!MULTI && tid == 0) add_global(a0.acc, gacc);
+  __syncthreads();
+  if (s_hub) hub_flush(s_hub, a0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1060,7 +1110,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
     }
     if (nm) {
       PhaseScope ph(PB_PHASE_MEDIUM, s);
-      const size_t smem = 2 * MB_CAP * sizeof(uint32_t);
+      const size_t smem = (MB_CAP + MB_CAP / 2) * sizeof(uint32_t);
       PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE, false>, MB_THREADS, smem);
@@ -1435,7 +1485,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
   PB_CUDA(cudaFuncSetAttribute(k_light<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t))));
   PB_CUDA(cudaFuncSetAttribute(k_medium<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(2 * MB_CAP * sizeof(uint32_t))));
+                               (int)((MB_CAP + MB_CAP / 2) * sizeof(uint32_t))));
   PB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   pb_status st = PB_OK;
   do {
@@ -1459,7 +1509,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch light launch", __FILE__, __LINE__); break; }
     }
     if (b->nm) {
-      const size_t smem = 2 * MB_CAP * sizeof(uint32_t);
+      const size_t smem = (MB_CAP + MB_CAP / 2) * sizeof(uint32_t);
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, false, true>, MB_THREADS, smem);
       unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
