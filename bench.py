@@ -71,7 +71,8 @@ def parse():
                          "vs one launch per graph; serving: Poisson request stream")
     ap.add_argument("--graphs", type=int, default=1024)
     ap.add_argument("--workload", default="cl2", choices=sorted(WORKLOADS))
-    ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree"])
+    ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree", "complement_degeneracy",
+                                                        "approx_complement_degeneracy"])
     ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
     ap.add_argument("--outputs", default="all", choices=["all", "global", "vertex"])
     ap.add_argument("--retrieval", default="auto", choices=["low", "high", "auto"])

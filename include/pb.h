@@ -46,11 +46,18 @@ typedef struct pb_graph pb_graph; /* opaque, library-owned */
  *                 wedges (ties: U); ids in order within a side.
  *  DEGREE:        decreasing degree (Chiba-Nishizeki); ties by global id.
  *  APPROX_DEGREE: decreasing floor(log2 degree); ties keep global-id order;
- *                 degree-0 vertices last. */
+ *                 degree-0 vertices last.
+ *  COMPLEMENT_DEGENERACY: peeling rounds; each round ranks next every
+ *                 remaining vertex whose degree in the subgraph induced by
+ *                 the remaining vertices is the largest (ties: global id).
+ *  APPROX_COMPLEMENT_DEGENERACY: the same with floor(log2 degree) classes
+ *                 (at most 33 rounds). */
 typedef enum {
   PB_RANK_SIDE = 0,
   PB_RANK_DEGREE = 1,
-  PB_RANK_APPROX_DEGREE = 2
+  PB_RANK_APPROX_DEGREE = 2,
+  PB_RANK_COMPLEMENT_DEGENERACY = 3,
+  PB_RANK_APPROX_COMPLEMENT_DEGENERACY = 4
 } pb_rank_kind;
 
 /* Wedge aggregation methods of Sec. "Wedge aggregation".
@@ -109,7 +116,7 @@ typedef struct {
   uint64_t m_in;       /* edges given, duplicates included */
   uint64_t m;          /* distinct edges */
   uint32_t max_deg_U, max_deg_V;
-  int32_t rank_kind;   /* pb_rank_kind, 3 = custom ranking, -1 = not ranked */
+  int32_t rank_kind;   /* pb_rank_kind, 5 = custom ranking, -1 = not ranked */
   uint64_t W;          /* wedges retrieved under the current ranking */
   uint64_t max_wedges_x1; /* largest wedge count of one lower-ranked endpoint */
   uint64_t device_bytes;  /* device memory held by the graph (scratch included) */

@@ -36,8 +36,9 @@ _SO = os.path.join(_BUILD, "libpboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RANK_SIDE, RANK_DEGREE, RANK_APPROX_DEGREE = 0, 1, 2
-RANK_KINDS = {"side": RANK_SIDE, "degree": RANK_DEGREE, "approx_degree": RANK_APPROX_DEGREE}
+RANK_SIDE, RANK_DEGREE, RANK_APPROX_DEGREE, RANK_CODEGEN, RANK_APPROX_CODEGEN = 0, 1, 2, 3, 4
+RANK_KINDS = {"side": RANK_SIDE, "degree": RANK_DEGREE, "approx_degree": RANK_APPROX_DEGREE,
+              "complement_degeneracy": RANK_CODEGEN, "approx_complement_degeneracy": RANK_APPROX_CODEGEN}
 
 
 class OracleError(RuntimeError):

@@ -103,3 +103,33 @@ def butterflies_listed(nU: int, nV: int, u, v):
         for b1, b2 in combinations(common, 2):
             out.append(((a1, a2), (b1, b2)))
     return out
+
+
+def complement_degeneracy_rank(nU: int, nV: int, u, v, approx: bool = False):
+    """Peeling rounds written out with sets: every round removes all
+    remaining vertices of largest current degree (or largest current
+    floor(log2 degree), degree 0 lowest); ties within a round by global id."""
+    n = nU + nV
+    nbr = [set() for _ in range(n)]
+    for a, b in zip(np.asarray(u).tolist(), np.asarray(v).tolist()):
+        nbr[a].add(nU + b)
+        nbr[nU + b].add(a)
+    remaining = set(range(n))
+    rank = np.empty(n, np.int64)
+    nxt = 0
+
+    def key(x):
+        d = len(nbr[x] & remaining)
+        if not approx:
+            return d
+        return d.bit_length() - 1 if d > 0 else -1
+
+    while remaining:
+        best = max(key(x) for x in remaining)
+        front = sorted(x for x in remaining if key(x) == best)
+        for x in front:
+            rank[x] = nxt
+            nxt += 1
+        remaining -= set(front)
+    return rank
+

@@ -26,14 +26,16 @@
  *   degree order: key (-deg, global id); approximate degree order: key
  *   (-floor(log2 deg), global id) with degree-0 vertices last; side order:
  *   the side whose vertices as endpoints give fewer wedges comes first
- *   (ties: U), ids in order within a side.  rank 0 is first.
+ *   (ties: U), ids in order within a side; complement degeneracy orders:
+ *   peeling rounds, ties within a round by global id.  rank 0 is first.
  */
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_RANK_SIDE = 0, ORC_RANK_DEGREE = 1, ORC_RANK_APPROX_DEGREE = 2 };
+enum { ORC_RANK_SIDE = 0, ORC_RANK_DEGREE = 1, ORC_RANK_APPROX_DEGREE = 2, ORC_RANK_CODEGEN = 3,
+       ORC_RANK_APPROX_CODEGEN = 4 };
 enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_NOMEM = 2, ORC_ERR_OVERFLOW = 6 };
 
 /* ------------------------------------------------------------------ */
@@ -134,10 +136,65 @@ static uint32_t floor_log2_u32(uint32_t d) {
   return r;
 }
 
+/* Complement degeneracy order (Sec. "Ranking"): peeling rounds, each removing
+ * every remaining vertex whose current degree (in the subgraph induced by the
+ * remaining vertices) is the largest -- or, for the approximate order, whose
+ * current floor(log2 degree) is the largest, degree 0 below every class.
+ * Vertices removed in the same round are ranked in global-id order. */
+static int codegen_rank(const bgraph_t *g, int approx, uint32_t *rank) {
+  uint32_t nU = g->nU, nV = g->nV;
+  uint64_t n = (uint64_t)nU + nV;
+  uint64_t *off = (uint64_t *)calloc(n + 1, sizeof(uint64_t));
+  uint32_t *nb = (uint32_t *)malloc(sizeof(uint32_t) * (2 * g->m + 1));
+  uint64_t *cur = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
+  uint32_t *d = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+  uint8_t *gone = (uint8_t *)calloc(n ? n : 1, 1);
+  uint32_t *front = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+  if (!off || !nb || !cur || !d || !gone || !front) {
+    free(off); free(nb); free(cur); free(d); free(gone); free(front);
+    return ORC_ERR_NOMEM;
+  }
+  for (uint64_t x = 0; x < n; x++) off[x + 1] = off[x] + g->deg[x];
+  memcpy(cur, off, sizeof(uint64_t) * (n + 1));
+  for (uint32_t i = 0; i < nU; i++)
+    for (uint64_t e = g->uoff[i]; e < g->uoff[i + 1]; e++) {
+      uint32_t j = nU + g->uadj[e];
+      nb[cur[i]++] = j;
+      nb[cur[j]++] = i;
+    }
+  for (uint64_t x = 0; x < n; x++) d[x] = g->deg[x];
+  uint64_t next = 0;
+  while (next < n) {
+    int64_t best = -2;
+    for (uint64_t x = 0; x < n; x++) {
+      if (gone[x]) continue;
+      int64_t key = approx ? (d[x] ? (int64_t)floor_log2_u32(d[x]) : -1) : (int64_t)d[x];
+      if (key > best) best = key;
+    }
+    uint64_t nf = 0;
+    for (uint64_t x = 0; x < n; x++) {
+      if (gone[x]) continue;
+      int64_t key = approx ? (d[x] ? (int64_t)floor_log2_u32(d[x]) : -1) : (int64_t)d[x];
+      if (key == best) front[nf++] = (uint32_t)x;
+    }
+    for (uint64_t f = 0; f < nf; f++) { rank[front[f]] = (uint32_t)(next + f); gone[front[f]] = 1; }
+    next += nf;
+    for (uint64_t f = 0; f < nf; f++) {
+      uint32_t x = front[f];
+      for (uint64_t a = off[x]; a < off[x + 1]; a++)
+        if (!gone[nb[a]]) d[nb[a]]--;
+    }
+  }
+  free(off); free(nb); free(cur); free(d); free(gone); free(front);
+  return ORC_OK;
+}
+
 /* rank[id] for id in [0, n). */
 static int make_rank(const bgraph_t *g, int kind, uint32_t *rank) {
   uint32_t nU = g->nU, nV = g->nV;
   uint64_t n = (uint64_t)nU + nV;
+  if (kind == ORC_RANK_CODEGEN || kind == ORC_RANK_APPROX_CODEGEN)
+    return codegen_rank(g, kind == ORC_RANK_APPROX_CODEGEN, rank);
   if (kind == ORC_RANK_SIDE) {
     /* Wedges retrieved when side X holds the endpoints: every pair of
      * neighbours of a centre on the other side, i.e. sum over centres y not in
@@ -330,7 +387,7 @@ int orc_rank(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, const u
   bgraph_t g;
   int rc = bgraph_build(nU, nV, m_in, u, v, &g);
   if (rc) return rc;
-  if (kind < 0 || kind > 2) { bgraph_free(&g); return ORC_ERR_INVALID; }
+  if (kind < 0 || kind > 4) { bgraph_free(&g); return ORC_ERR_INVALID; }
   rc = make_rank(&g, kind, rank_out);
   bgraph_free(&g);
   return rc;
@@ -376,7 +433,7 @@ int orc_count_range(uint32_t nU, uint32_t nV, uint64_t m_in, const uint32_t *u, 
     }
     free(seen);
   } else {
-    if (kind < 0 || kind > 2) { free(rank); bgraph_free(&g); return ORC_ERR_INVALID; }
+    if (kind < 0 || kind > 4) { free(rank); bgraph_free(&g); return ORC_ERR_INVALID; }
     rc = make_rank(&g, kind, rank);
     if (rc) { free(rank); bgraph_free(&g); return rc; }
   }

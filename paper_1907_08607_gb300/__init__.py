@@ -24,7 +24,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpb.so")
 
-RANKS = {"side": 0, "degree": 1, "approx_degree": 2}
+RANKS = {"side": 0, "degree": 1, "approx_degree": 2, "complement_degeneracy": 3,
+         "approx_complement_degeneracy": 4}
 AGGS = {"sort": 0, "hash": 1, "hist": 2, "batch": 3, "auto": 4}
 RETRIEVALS = {"low": 0, "high": 1, "auto": 2}
 STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 4: "PB_ERR_SCRATCH",

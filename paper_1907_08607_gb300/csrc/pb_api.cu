@@ -262,7 +262,8 @@ pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32
 pb_status pb_rank(pb_graph *g, pb_rank_kind kind, void *stream) {
   clear_error();
   if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
-  if (kind < PB_RANK_SIDE || kind > PB_RANK_APPROX_DEGREE) return fail(PB_ERR_INVALID, "unknown rank kind %d", (int)kind);
+  if (kind < PB_RANK_SIDE || kind > PB_RANK_APPROX_COMPLEMENT_DEGENERACY)
+    return fail(PB_ERR_INVALID, "unknown rank kind %d", (int)kind);
   DeviceGuard dg(g->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   {
@@ -282,7 +283,7 @@ pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, vo
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   {
     PhaseScope ph(PB_PHASE_RANK, s);
-    PB_TRY(rank_graph(g, 3, rank_of, on_device, s));
+    PB_TRY(rank_graph(g, 5, rank_of, on_device, s));
     ph.finish(s);
   }
   PB_CUDA(cudaStreamSynchronize(s));

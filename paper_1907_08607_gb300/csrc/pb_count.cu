@@ -1401,7 +1401,7 @@ void make_plan(const pb_graph *g, pb_plan_t *plan) {
   plan->W_rank = g->W;
   plan->f_side = w_side ? (static_cast<double>(w_side) - static_cast<double>(g->W)) / static_cast<double>(w_side) : 0.0;
   // side order when the ranking saves under 10% of its wedges (Table 3's rule)
-  plan->rank_kind = plan->f_side < 0.1 ? PB_RANK_SIDE : (g->rank_kind >= 0 && g->rank_kind <= 2 ? g->rank_kind
+  plan->rank_kind = plan->f_side < 0.1 ? PB_RANK_SIDE : (g->rank_kind >= 0 && g->rank_kind <= 4 ? g->rank_kind
                                                                                                    : PB_RANK_DEGREE);
   const bool high = g->maxw_rev <= g->maxw;
   plan->retrieval = high ? PB_RETRIEVE_HIGH : PB_RETRIEVE_LOW;

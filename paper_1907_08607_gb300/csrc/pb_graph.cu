@@ -215,6 +215,118 @@ __global__ void k_custom_rank(const uint32_t *__restrict__ rank_of, uint64_t n, 
 }
 
 // ---------------------------------------------------------------------------
+// Complement degeneracy orders (peeling rounds on the device, driven from the
+// host: at most 33 rounds for the approximate order).
+
+__global__ void k_id_csr(const uint32_t *__restrict__ eu, const uint32_t *__restrict__ ev, uint64_t m, uint32_t nU,
+                         uint32_t *__restrict__ cur, uint32_t *__restrict__ nb) {
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t a = eu[e], b = nU + ev[e];
+    nb[atomicAdd(&cur[a], 1u)] = b;
+    nb[atomicAdd(&cur[b], 1u)] = a;
+  }
+}
+
+__device__ __forceinline__ uint32_t cd_key(uint32_t d, int approx) {
+  return approx ? (d ? 32u - __clz(d) : 0u) : d;  // floor(log2 d) + 1, 0 for degree 0
+}
+
+__global__ void k_cd_max(const uint32_t *__restrict__ d, const uint32_t *__restrict__ rank, uint64_t n, int approx,
+                         uint32_t *out) {
+  uint32_t mx = 0;
+  bool any = false;
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x)
+    if (rank[x] == 0xffffffffu) {
+      uint32_t k = cd_key(d[x], approx);
+      mx = k > mx ? k : mx;
+      any = true;
+    }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+  if (__any_sync(FULL, any) && lane_id() == 0) atomicMax(out, mx + 1);  // +1: 0 means nothing left
+}
+
+__global__ void k_cd_flag(const uint32_t *__restrict__ d, const uint32_t *__restrict__ rank, uint64_t n, int approx,
+                          uint32_t best, uint32_t *__restrict__ flag) {
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x)
+    flag[x] = (rank[x] == 0xffffffffu && cd_key(d[x], approx) == best) ? 1u : 0u;
+}
+
+__global__ void k_cd_assign(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, uint64_t n,
+                            uint32_t base, uint32_t *__restrict__ rank, uint32_t *__restrict__ order) {
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x)
+    if (flag[x]) {
+      uint32_t r = base + pos[x];
+      rank[x] = r;
+      order[r] = static_cast<uint32_t>(x);
+    }
+}
+
+// One warp per vertex peeled this round: its remaining neighbours lose a degree.
+__global__ void k_cd_peel(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ off,
+                          const uint32_t *__restrict__ nb, const uint32_t *__restrict__ rank, uint64_t n,
+                          uint32_t *__restrict__ d) {
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * blockDim.x / 32;
+  for (uint64_t x = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32; x < n; x += warps) {
+    if (!flag[x]) continue;
+    for (uint32_t a = off[x] + lane_id(); a < off[x + 1]; a += 32) {
+      uint32_t z = nb[a];
+      if (rank[z] == 0xffffffffu) atomicSub(&d[z], 1u);
+    }
+  }
+}
+
+static pb_status codegen_rank(pb_graph *g, int approx, cudaStream_t s) {
+  const uint64_t n = g->n, m = g->m;
+  uint32_t *off = nullptr, *cur = nullptr, *nb = nullptr, *d = nullptr, *flag = nullptr, *pos = nullptr,
+           *dmax = nullptr;
+  pb_status st = PB_OK;
+  do {
+    if ((st = dalloc_t(&off, n + 1, s)) != PB_OK || (st = dalloc_t(&cur, n + 1, s)) != PB_OK ||
+        (st = dalloc_t(&nb, 2 * m + 1, s)) != PB_OK || (st = dalloc_t(&d, n + 1, s)) != PB_OK ||
+        (st = dalloc_t(&flag, n + 1, s)) != PB_OK || (st = dalloc_t(&pos, n + 1, s)) != PB_OK ||
+        (st = dalloc_t(&dmax, 1, s)) != PB_OK) break;
+    if ((st = scan_u32(g->deg, off, n, s)) != PB_OK) break;
+    if (cudaMemcpyAsync(cur, off, (n + 1) * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d, g->deg, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(g->rank, 0xff, (n + 1) * 4, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "copy"); break; }
+    if (m) {
+      k_id_csr<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, cur, nb);
+      count_launch();
+    }
+    uint64_t done = 0;
+    for (uint64_t round = 0; done < n; round++) {
+      if (round > n + 1) { st = fail(PB_ERR_CUDA, "peeling made no progress"); break; }
+      uint32_t best1 = 0, cnt = 0;
+      if (cudaMemsetAsync(dmax, 0, 4, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      k_cd_max<<<grid_for(n, 256, 4096), 256, 0, s>>>(d, g->rank, n, approx, dmax);
+      count_launch();
+      if (cudaMemcpyAsync(&best1, dmax, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "round readback"); break; }
+      if (best1 == 0) { st = fail(PB_ERR_CUDA, "peeling lost vertices"); break; }
+      k_cd_flag<<<grid_for(n, 256, 8192), 256, 0, s>>>(d, g->rank, n, approx, best1 - 1, flag);
+      count_launch();
+      if ((st = scan_u32(flag, pos, n, s)) != PB_OK) break;
+      k_cd_assign<<<grid_for(n, 256, 8192), 256, 0, s>>>(flag, pos, n, static_cast<uint32_t>(done), g->rank,
+                                                         g->order);
+      count_launch();
+      k_cd_peel<<<grid_for(n * 32, 256, 8192), 256, 0, s>>>(flag, off, nb, g->rank, n, d);
+      count_launch();
+      if (cudaMemcpyAsync(&cnt, pos + n, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "round readback"); break; }
+      if (cnt == 0) { st = fail(PB_ERR_CUDA, "empty peeling round"); break; }
+      done += cnt;
+    }
+  } while (0);
+  dfree(off, s); dfree(cur, s); dfree(nb, s); dfree(d, s); dfree(flag, s); dfree(pos, s); dfree(dmax, s);
+  return st;
+}
+
+// ---------------------------------------------------------------------------
 // Renaming + adjacency.  Labels: U vertices [0, nU), V vertices [nU, n), each
 // side in rank order.  Every canonical edge e = (u, v) gives two arcs: 2e from
 // u to v and 2e+1 back.  Keys (label(src) << bitsN) | (maxrank - rank(nbr))
@@ -429,6 +541,8 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       if (hacc[0]) { st = fail(PB_ERR_INVALID, "rank_of is not a permutation of [0, %llu)", (unsigned long long)n); break; }
       dfree(tmp, s);
       tmp = nullptr;
+    } else if (kind == PB_RANK_COMPLEMENT_DEGENERACY || kind == PB_RANK_APPROX_COMPLEMENT_DEGENERACY) {
+      if ((st = codegen_rank(g, kind == PB_RANK_APPROX_COMPLEMENT_DEGENERACY, s)) != PB_OK) break;
     } else if (kind == PB_RANK_SIDE) {
       int u_first = g->w_side_U <= g->w_side_V;
       if (n) {
@@ -514,7 +628,7 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
     g->W = hW;
     g->maxw = hacc[0];
     g->maxw_rev = hacc[1];
-    g->rank_kind = rank_of ? 3 : kind;
+    g->rank_kind = rank_of ? 5 : kind;
   } while (0);
   dfree(keys, s); dfree(vals, s); dfree(tmp, s); dfree(drank, s); dfree(acc, s); dfree(wc, s);
   dfree(lrank, s); dfree(cu, s);

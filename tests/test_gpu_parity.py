@@ -11,7 +11,7 @@ from tests._fixtures import fig2_graph, fig2_rank, random_rank, tiny_graphs
 
 pytestmark = pytest.mark.gpu
 
-RANKS = ["side", "degree", "approx_degree"]
+RANKS = ["side", "degree", "approx_degree", "complement_degeneracy", "approx_complement_degeneracy"]
 AGGS = ["hash", "hist", "batch", "sort", "auto"]
 
 

@@ -219,3 +219,32 @@ def test_degenerate_inputs():
     # ids out of range are rejected
     with pytest.raises(oracle.OracleError):
         oracle.count(2, 2, np.array([2], np.uint32), np.array([0], np.uint32))
+
+
+# ----------------------------------------------------------------- complement degeneracy
+@pytest.mark.parametrize("approx", [False, True])
+def test_complement_degeneracy_matches_brute_and_bounds(tiny, approx):
+    kind = "approx_complement_degeneracy" if approx else "complement_degeneracy"
+    for g in tiny[:25]:
+        r = oracle.rank(g.nU, g.nV, g.u, g.v, kind).astype(np.int64)
+        np.testing.assert_array_equal(r, brute.complement_degeneracy_rank(g.nU, g.nV, g.u, g.v, approx))
+        # the work bound of the paper's proof: for an edge (x, y) with x ranked
+        # first, y's neighbours ranked above x number at most deg(x)
+        # (2 deg(x) for the approximate order)
+        n = g.nU + g.nV
+        deg = np.concatenate([np.bincount(g.u, minlength=g.nU), np.bincount(g.v, minlength=g.nV)])
+        nb = [[] for _ in range(n)]
+        for a, b in set(zip(g.u.tolist(), g.v.tolist())):
+            nb[a].append(g.nU + b)
+            nb[g.nU + b].append(a)
+        for x in range(n):
+            for y in nb[x]:
+                if r[x] < r[y]:
+                    above = sum(1 for z in nb[y] if r[z] > r[x])
+                    assert above <= (2 if approx else 1) * deg[x]
+        c = oracle.count(g.nU, g.nV, g.u, g.v, kind=kind)
+        assert c.W == brute.wedges(g.nU, g.nV, g.u, g.v, r)
+        glob, pv, pe = brute.counts(g.nU, g.nV, g.u, g.v)
+        assert c.global_count == glob
+        np.testing.assert_array_equal(c.per_vertex.astype(np.int64), pv)
+
