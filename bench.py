@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
     ap.add_argument("--outputs", default="all", choices=["all", "global", "vertex"])
     ap.add_argument("--retrieval", default="auto", choices=["low", "high", "auto"])
+    ap.add_argument("--butterfly", default="atomic", choices=["atomic", "sort"],
+                    help="butterfly aggregation: atomic adds or sort re-aggregation (needs --agg sort)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -256,7 +258,7 @@ def run_gb300(args):
     def step():
         G = pb.Graph.from_edges(g.nU, g.nV, du, dv)
         G.rank(args.rank)
-        G.set_retrieval(args.retrieval)
+        G.set_retrieval(args.retrieval).set_butterfly_aggregation(args.butterfly)
         c = G.count_all(args.agg, on_device=True, out=outs, vertex=args.outputs != "global",
                         edge=args.outputs == "all")
         state["W"] = G.wedges
@@ -307,7 +309,7 @@ def run_gb300(args):
         def step_host():
             G = pb.Graph.from_edges(g.nU, g.nV, hu, hv)
             G.rank(args.rank)
-            G.set_retrieval(args.retrieval)
+            G.set_retrieval(args.retrieval).set_butterfly_aggregation(args.butterfly)
             G.count_all(args.agg, on_device=False, out=hout)
             G.free()
 
@@ -354,7 +356,7 @@ def run_gb300(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "rank": args.rank, "agg": args.agg,
-                   "retrieval": args.retrieval,
+                   "retrieval": args.retrieval, "butterfly_aggregation": args.butterfly,
                    "outputs": {"all": "global+per-vertex+per-edge", "global": "global",
                                "vertex": "global+per-vertex"}[args.outputs], "W": W, "butterflies": state["global"],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (400 MB edge list)"},

@@ -100,6 +100,19 @@ typedef enum {
   PB_RETRIEVE_AUTO = 2
 } pb_retrieval;
 
+/* Butterfly aggregation (Sec. "Butterfly aggregation"): how the per-vertex and
+ * per-edge contributions found by wedge aggregation reach their counters.
+ *  ATOMIC: each contribution is added with an atomic add (the default; the
+ *          paper's recommended option).
+ *  SORT:   re-aggregation: contributions are written out as (vertex or edge,
+ *          value) pairs, radix-sorted by key and summed per key, and every
+ *          counter is then written once per chunk of wedges, without atomics.
+ *          Needs wedge aggregation PB_AGG_SORT; counts are identical. */
+typedef enum {
+  PB_BFLY_ATOMIC = 0,
+  PB_BFLY_SORT = 1
+} pb_bfly_agg;
+
 typedef enum {
   PB_OK = 0,
   PB_ERR_INVALID = 1,  /* bad argument, id out of range, size over a limit */
@@ -148,6 +161,12 @@ pb_status pb_rank_custom(pb_graph *g, const uint32_t *rank_of, int on_device, vo
 
 /* Selects the wedge owner used by later counts on g (default AUTO). */
 pb_status pb_set_retrieval(pb_graph *g, pb_retrieval r);
+
+/* Selects the butterfly aggregation used by later counts on g (default
+ * ATOMIC).  PB_ERR_INVALID for an unknown value; a later count with
+ * PB_BFLY_SORT and a wedge aggregation other than PB_AGG_SORT fails with
+ * PB_ERR_INVALID. */
+pb_status pb_set_butterfly_aggregation(pb_graph *g, pb_bfly_agg b);
 
 /* Writes rank_of[x] for every global id x (host or device). */
 pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream);

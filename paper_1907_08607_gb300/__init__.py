@@ -28,6 +28,7 @@ RANKS = {"side": 0, "degree": 1, "approx_degree": 2, "complement_degeneracy": 3,
          "approx_complement_degeneracy": 4}
 AGGS = {"sort": 0, "hash": 1, "hist": 2, "batch": 3, "auto": 4}
 RETRIEVALS = {"low": 0, "high": 1, "auto": 2}
+BUTTERFLY_AGGS = {"atomic": 0, "sort": 1}
 STATUS = {0: "PB_OK", 1: "PB_ERR_INVALID", 2: "PB_ERR_NOMEM", 3: "PB_ERR_CUDA", 4: "PB_ERR_SCRATCH",
           5: "PB_ERR_TIMEOUT", 6: "PB_ERR_OVERFLOW"}
 
@@ -38,7 +39,7 @@ ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ran
                "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc",
                "pb_set_retrieval", "pb_count_owner_range", "pb_wedge_prefix", "pb_sparsify", "pb_autotune",
                "pb_batch_create", "pb_batch_run", "pb_batch_globals", "pb_batch_vertex", "pb_batch_wedges",
-               "pb_batch_free"]
+               "pb_batch_free", "pb_set_butterfly_aggregation"]
 
 PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
@@ -116,6 +117,8 @@ def load_library(path: str = LIB_PATH):
         lib.pb_count_noalloc.restype = i32
         lib.pb_set_retrieval.argtypes = [vp, i32]
         lib.pb_set_retrieval.restype = i32
+        lib.pb_set_butterfly_aggregation.argtypes = [vp, i32]
+        lib.pb_set_butterfly_aggregation.restype = i32
         lib.pb_count_owner_range.argtypes = [vp, i32, u64, u32, u32, u64p, vp, vp, vp, i32, vp]
         lib.pb_count_owner_range.restype = i32
         lib.pb_wedge_prefix.argtypes = [vp, vp, i32, vp]
@@ -296,6 +299,12 @@ class Graph:
         """Wedge owner for later counts: "low" (Algorithm 2), "high" (the
         cache optimisation) or "auto"."""
         _check(load_library().pb_set_retrieval(self._h, RETRIEVALS[which]))
+        return self
+
+    def set_butterfly_aggregation(self, which: str = "atomic") -> "Graph":
+        """How per-vertex / per-edge contributions reach their counters:
+        "atomic" adds, or "sort" re-aggregation (needs agg="sort")."""
+        _check(load_library().pb_set_butterfly_aggregation(self._h, BUTTERFLY_AGGS[which]))
         return self
 
     def autotune(self) -> dict:

@@ -299,6 +299,14 @@ pb_status pb_set_retrieval(pb_graph *g, pb_retrieval r) {
   return PB_OK;
 }
 
+pb_status pb_set_butterfly_aggregation(pb_graph *g, pb_bfly_agg b) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  if (b != PB_BFLY_ATOMIC && b != PB_BFLY_SORT) return fail(PB_ERR_INVALID, "unknown butterfly aggregation %d", (int)b);
+  g->butterfly_agg = b;
+  return PB_OK;
+}
+
 pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream) {
   clear_error();
   if (!g || !rank_of) return fail(PB_ERR_INVALID, "graph or rank_of is NULL");

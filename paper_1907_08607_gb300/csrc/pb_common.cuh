@@ -48,6 +48,7 @@ struct pb_graph {
   uint64_t maxw = 0;          // max wedges of one lower-ranked endpoint
   uint64_t maxw_rev = 0;      // max wedges of one higher-ranked endpoint
   int retrieval = PB_RETRIEVE_AUTO;
+  int butterfly_agg = PB_BFLY_ATOMIC;
   uint64_t w_side_U = 0, w_side_V = 0;  // wedges with endpoints in U / in V (side order)
 
   // Aggregation scratch, grown on demand and kept until pb_graph_free.

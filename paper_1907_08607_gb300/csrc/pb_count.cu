@@ -799,12 +799,44 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *a, uint32_t 
   return lo;
 }
 
-template <bool PV, bool PE, bool EMIT>
+// Butterfly aggregation by re-aggregation (Sec. "Butterfly aggregation", the
+// alternative to atomic adds): contributions are appended as (key, value)
+// pairs, then sorted by key and summed per key, so each counter is written
+// once.  Keys are vertex labels (per-vertex) or adjacency slots (per-edge).
+struct Sink {
+  uint64_t *vkey, *ekey;
+  unsigned long long *vval, *eval;
+  unsigned long long *vcnt, *ecnt;  // append cursors
+  uint64_t vcap, ecap;
+};
+
+// Warp-aggregated append; every lane of the warp calls it.
+__device__ __forceinline__ void sink_put(uint64_t *keys, unsigned long long *vals, unsigned long long *cursor,
+                                         uint64_t cap, uint64_t key, unsigned long long v, bool act,
+                                         unsigned long long *err) {
+  const uint32_t bm = __ballot_sync(FULL, act);
+  if (!bm) return;
+  const uint32_t leader = __ffs(bm) - 1;
+  unsigned long long b0 = 0;
+  if (lane_id() == leader) b0 = atomicAdd(cursor, static_cast<unsigned long long>(__popc(bm)));
+  b0 = __shfl_sync(FULL, b0, leader);
+  if (act) {
+    const unsigned long long at = b0 + __popc(bm & lanemask_lt());
+    if (at < cap) {
+      keys[at] = key;
+      vals[at] = v;
+    } else {
+      atomicOr(err, 64ull);
+    }
+  }
+}
+
+template <bool PV, bool PE, bool EMIT, bool RE>
 __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, uint32_t hi, uint64_t wbase,
                                                           int bitsN, uint64_t *__restrict__ keys,
                                                           const uint64_t *__restrict__ ukey,
                                                           const uint32_t *__restrict__ ud,
-                                                          const uint32_t *__restrict__ seg) {
+                                                          const uint32_t *__restrict__ seg, Sink sk) {
   __shared__ uint32_t s_incl[MB_THREADS], s_ex[MB_THREADS], s_oy[MB_THREADS];
   __shared__ unsigned long long s_sum[MB_THREADS];
   __shared__ uint32_t s_w[33];
@@ -835,11 +867,11 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
       __syncthreads();
       for (uint32_t wb = 0; wb < tot; wb += MB_THREADS) {
         const uint32_t wi = wb + tid;
-        uint32_t src = 0;
+        uint32_t src = 0, slot = 0;
         unsigned long long t = 0;
         if (wi < tot) {
           src = block_find(s_incl, MB_THREADS, wi);
-          uint32_t slot = s_oy[src] + (wi - s_ex[src]);
+          slot = s_oy[src] + (wi - s_ex[src]);
           uint32_t x2 = a.adj[slot];
           if (EMIT) {
             out[done + wi] = kx | x2;
@@ -849,20 +881,26 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
             if (d == 0) atomicOr(&a.acc[ACC_ERR], 32ull);
             if (d > 1) {
               t = d - 1;
-              if (PE) atomicAdd(&a.es[slot], t);
+              if (PE && !RE) atomicAdd(&a.es[slot], t);
             }
           }
         }
-        if (!EMIT) warp_run_add(s_sum, src, t);
+        if (!EMIT) {
+          if (PE && RE) sink_put(sk.ekey, sk.eval, sk.ecnt, sk.ecap, slot, t, t != 0, &a.acc[ACC_ERR]);
+          warp_run_add(s_sum, src, t);
+        }
       }
       __syncthreads();
-      if (!EMIT && v) {
-        unsigned long long sm = s_sum[tid];
-        if (sm) {
+      if (!EMIT) {
+        unsigned long long sm = v ? s_sum[tid] : 0;
+        if (RE) {
+          if (PV) sink_put(sk.vkey, sk.vval, sk.vcnt, sk.vcap, y, sm, sm != 0, &a.acc[ACC_ERR]);
+          if (PE) sink_put(sk.ekey, sk.eval, sk.ecnt, sk.ecap, base + i, sm, sm != 0, &a.acc[ACC_ERR]);
+        } else if (sm) {
           if (PV) atomicAdd(&a.pv[y], sm);
           if (PE) atomicAdd(&a.es[base + i], sm);
-          s_sum[tid] = 0;
         }
+        if (v) s_sum[tid] = 0;
       }
       done += tot;
       __syncthreads();
@@ -883,20 +921,31 @@ __global__ void k_runs(const uint64_t *__restrict__ keys, const uint32_t *__rest
   }
 }
 
-template <bool PV>
+template <bool PV, bool RE>
 __global__ void k_run_sums(CArgs a, const uint64_t *__restrict__ ukey, const uint32_t *__restrict__ rstart,
-                           uint32_t nr, uint32_t cnt, uint32_t lo, int bitsN, uint32_t *__restrict__ ud) {
+                           uint32_t nr, uint32_t cnt, uint32_t lo, int bitsN, uint32_t *__restrict__ ud, Sink sk) {
   __shared__ unsigned long long s_w64[33];
   const uint64_t mask = (uint64_t(1) << bitsN) - 1;
   unsigned long long acc = 0;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
-    uint32_t d = (r + 1 < nr ? rstart[r + 1] : cnt) - rstart[r];
-    ud[r] = d;
-    unsigned long long b = static_cast<unsigned long long>(d) * (d - 1) / 2;
-    acc += b;
-    if (PV && b) {
-      atomicAdd(&a.pv[lo + static_cast<uint32_t>(ukey[r] >> bitsN)], b);
-      atomicAdd(&a.pv[static_cast<uint32_t>(ukey[r] & mask)], b);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t rb = blockIdx.x * blockDim.x; rb < nr; rb += stride) {  // block-uniform trip count
+    const uint32_t r = rb + threadIdx.x;
+    unsigned long long b = 0;
+    uint32_t k1 = 0, k2 = 0;
+    if (r < nr) {
+      uint32_t d = (r + 1 < nr ? rstart[r + 1] : cnt) - rstart[r];
+      ud[r] = d;
+      b = static_cast<unsigned long long>(d) * (d - 1) / 2;
+      acc += b;
+      k1 = lo + static_cast<uint32_t>(ukey[r] >> bitsN);
+      k2 = static_cast<uint32_t>(ukey[r] & mask);
+    }
+    if (PV && RE) {
+      sink_put(sk.vkey, sk.vval, sk.vcnt, sk.vcap, k1, b, b != 0, &a.acc[ACC_ERR]);
+      sink_put(sk.vkey, sk.vval, sk.vcnt, sk.vcap, k2, b, b != 0, &a.acc[ACC_ERR]);
+    } else if (PV && b) {
+      atomicAdd(&a.pv[k1], b);
+      atomicAdd(&a.pv[k2], b);
     }
   }
   unsigned long long tot = block_sum(acc, s_w64);
@@ -1206,13 +1255,75 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
   return st;
 }
 
-template <bool PV, bool PE>
+__global__ void k_iota(uint32_t *__restrict__ a, uint64_t n) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    a[i] = static_cast<uint32_t>(i);
+}
+
+__global__ void k_gather_u64(const unsigned long long *__restrict__ v, const uint32_t *__restrict__ idx, uint64_t n,
+                             uint64_t *__restrict__ out) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    out[i] = v[idx[i]];
+}
+
+// Run r (keys equal, sorted) adds its sum -- a difference of the prefix sums
+// -- to target[key]; keys are unique per run, so no atomics.
+__global__ void k_apply_runs(const uint64_t *__restrict__ ukey, const uint32_t *__restrict__ rstart, uint32_t nr,
+                             uint64_t cnt, const uint64_t *__restrict__ pre, unsigned long long *__restrict__ target) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+    const uint64_t b = rstart[r], e = r + 1 < nr ? rstart[r + 1] : cnt;
+    target[ukey[r]] += pre[e] - pre[b];
+  }
+}
+
+// Sorts (key, value) pairs by key and adds each key's total into target.
+static pb_status reaggregate(uint64_t *keys, unsigned long long *vals, uint64_t cnt, int bits,
+                             unsigned long long *target, cudaStream_t s) {
+  if (cnt == 0) return PB_OK;
+  uint32_t *idx = nullptr, *head = nullptr, *cid = nullptr, *rstart = nullptr;
+  uint64_t *sv = nullptr, *pre = nullptr, *ukey = nullptr;
+  pb_status st = PB_OK;
+  do {
+    if ((st = dalloc_t(&idx, cnt, s)) != PB_OK || (st = dalloc_t(&sv, cnt, s)) != PB_OK ||
+        (st = dalloc_t(&pre, cnt + 1, s)) != PB_OK || (st = dalloc_t(&head, cnt, s)) != PB_OK ||
+        (st = dalloc_t(&cid, cnt + 1, s)) != PB_OK || (st = dalloc_t(&ukey, cnt, s)) != PB_OK ||
+        (st = dalloc_t(&rstart, cnt, s)) != PB_OK) break;
+    k_iota<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(idx, cnt);
+    count_launch();
+    if ((st = radix_sort(keys, idx, cnt, bits, s)) != PB_OK) break;
+    k_gather_u64<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(vals, idx, cnt, sv);
+    count_launch();
+    if ((st = scan_u64(sv, pre, cnt, s)) != PB_OK) break;
+    k_heads<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(keys, cnt, head);
+    count_launch();
+    if ((st = scan_u32(head, cid, cnt, s)) != PB_OK) break;
+    uint32_t nr = 0;
+    if (cudaMemcpyAsync(&nr, cid + cnt, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "re-aggregation readback"); break; }
+    k_runs<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(keys, head, cid, cnt, ukey, rstart);
+    count_launch();
+    k_apply_runs<<<grid_for(nr, 256, 8192), 256, 0, s>>>(ukey, rstart, nr, cnt, pre, target);
+    count_launch();
+  } while (0);
+  dfree(idx, s); dfree(sv, s); dfree(pre, s); dfree(head, s); dfree(cid, s); dfree(ukey, s); dfree(rstart, s);
+  return st;
+}
+
+template <bool PV, bool PE, bool RE>
 static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t olo, uint64_t ohi,
                           cudaStream_t s) {
   const uint64_t n = g->n;
   const int bitsN = g->bitsN;
   // bytes per wedge: key, radix ping-pong key, head, run id, run key, run start, run d
-  const uint64_t per_wedge = 8 + 8 + 4 + 4 + 8 + 4 + 4;
+  uint64_t per_wedge = 8 + 8 + 4 + 4 + 8 + 4 + 4;
+  // Re-aggregation: at most 2 (key, value) pairs per wedge per output (run
+  // sums give 2 per run of >= 2 wedges; centres give one per wedge and one per
+  // (owner, centre) pair), plus reaggregate()'s temporaries for one sink
+  // (index, value, prefix, head, run id, run key, run start, radix ping-pong).
+  const uint64_t SINK_PER_WEDGE = 2;
+  if (RE) per_wedge += SINK_PER_WEDGE * (16 * ((PV ? 1 : 0) + (PE ? 1 : 0)) + 4 + 8 + 8 + 4 + 4 + 8 + 4 + 12);
   uint64_t cap = budget / per_wedge;
   if (cap > (uint64_t(1) << 31)) cap = uint64_t(1) << 31;
   const uint64_t maxw = a.rev ? g->maxw_rev : g->maxw;
@@ -1224,6 +1335,7 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
   pb_status st = PB_OK;
   uint64_t cap_alloc = cap < g->W ? cap : g->W;
   if (cap_alloc == 0) return PB_OK;
+  Sink sk{};
   do {
     if ((st = dalloc_t(&dchunk, 2, s)) != PB_OK) break;
     if ((st = dalloc_t(&keys, cap_alloc, s)) != PB_OK) break;
@@ -1232,6 +1344,16 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
     if ((st = dalloc_t(&ukey, cap_alloc, s)) != PB_OK) break;
     if ((st = dalloc_t(&rstart, cap_alloc, s)) != PB_OK) break;
     if ((st = dalloc_t(&ud, cap_alloc, s)) != PB_OK) break;
+    if (RE) {
+      sk.vcap = PV ? SINK_PER_WEDGE * cap_alloc : 0;
+      sk.ecap = PE ? SINK_PER_WEDGE * cap_alloc : 0;
+      if ((st = dalloc_t(&sk.vcnt, 2, s)) != PB_OK) break;
+      sk.ecnt = sk.vcnt + 1;
+      if (PV && ((st = dalloc_t(&sk.vkey, sk.vcap, s)) != PB_OK || (st = dalloc_t(&sk.vval, sk.vcap, s)) != PB_OK))
+        break;
+      if (PE && ((st = dalloc_t(&sk.ekey, sk.ecap, s)) != PB_OK || (st = dalloc_t(&sk.eval, sk.ecap, s)) != PB_OK))
+        break;
+    }
     const int sms = sm_count(g->device);
     uint32_t lo = static_cast<uint32_t>(olo);
     while (lo < ohi && st == PB_OK) {
@@ -1247,9 +1369,11 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
         if (cudaMemcpyAsync(&wbase, a.wpre + lo, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
         cudaStreamSynchronize(s);
         if (cudaMemsetAsync(a.acc + ACC_QMED, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        if (RE && cudaMemsetAsync(sk.vcnt, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         unsigned grid = static_cast<unsigned>(sms * 4);
         if (grid > hi - lo) grid = hi - lo;
-        k_sort_walk<PV, PE, true><<<grid, MB_THREADS, 0, s>>>(a, lo, hi, wbase, bitsN, keys, nullptr, nullptr, nullptr);
+        k_sort_walk<PV, PE, true, false><<<grid, MB_THREADS, 0, s>>>(a, lo, hi, wbase, bitsN, keys, nullptr, nullptr,
+                                                                     nullptr, sk);
         count_launch();
         int kbits = bits_for(hi - lo - 1) + bitsN;
         if ((st = radix_sort(keys, nullptr, cnt, kbits, s)) != PB_OK) break;
@@ -1261,8 +1385,8 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
             cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "run count readback"); break; }
         k_runs<<<grid_for(cnt, 256, 8192), 256, 0, s>>>(keys, head, cid, cnt, ukey, rstart);
         count_launch();
-        k_run_sums<PV><<<grid_for(nr, 256, 4096), 256, 0, s>>>(a, ukey, rstart, nr, static_cast<uint32_t>(cnt), lo,
-                                                               bitsN, ud);
+        k_run_sums<PV, RE><<<grid_for(nr, 256, 4096), 256, 0, s>>>(a, ukey, rstart, nr, static_cast<uint32_t>(cnt),
+                                                                   lo, bitsN, ud, sk);
         count_launch();
         if (PV || PE) {
           dfree(seg, s);
@@ -1271,8 +1395,19 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
           k_segments<<<grid_for(hi - lo + 1, 256, 4096), 256, 0, s>>>(ukey, nr, hi - lo, bitsN, seg);
           count_launch();
           if (cudaMemsetAsync(a.acc + ACC_QMED, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-          k_sort_walk<PV, PE, false><<<grid, MB_THREADS, 0, s>>>(a, lo, hi, wbase, bitsN, nullptr, ukey, ud, seg);
+          k_sort_walk<PV, PE, false, RE><<<grid, MB_THREADS, 0, s>>>(a, lo, hi, wbase, bitsN, nullptr, ukey, ud, seg,
+                                                                     sk);
           count_launch();
+        }
+        if (RE && (PV || PE)) {
+          // Butterfly re-aggregation of this chunk: sort the emitted pairs by
+          // key and add each key's total once.
+          unsigned long long hn[2] = {0, 0};
+          if (cudaMemcpyAsync(hn, sk.vcnt, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "sink count readback"); break; }
+          if (hn[0] > sk.vcap || hn[1] > sk.ecap) { st = fail(PB_ERR_SCRATCH, "re-aggregation sink overflow"); break; }
+          if (PV && (st = reaggregate(sk.vkey, sk.vval, hn[0], bits_for(n), a.pv, s)) != PB_OK) break;
+          if (PE && (st = reaggregate(sk.ekey, sk.eval, hn[1], bits_for(2 * g->m), a.es, s)) != PB_OK) break;
         }
         if (cudaGetLastError() != cudaSuccess) { st = fail(PB_ERR_CUDA, "sort aggregation kernels failed to launch"); break; }
       }
@@ -1281,12 +1416,15 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
   } while (0);
   dfree(dchunk, s); dfree(keys, s); dfree(head, s); dfree(cid, s); dfree(ukey, s); dfree(rstart, s);
   dfree(ud, s); dfree(seg, s);
+  dfree(sk.vcnt, s); dfree(sk.vkey, s); dfree(sk.vval, s); dfree(sk.ekey, s); dfree(sk.eval, s);
   return st;
 }
 
 pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut &o, cudaStream_t s) {
   if (g->rank_kind < 0) PB_TRY(rank_graph(g, PB_RANK_SIDE, nullptr, 0, s));
   if (agg < 0 || agg > PB_AGG_AUTO) return fail(PB_ERR_INVALID, "unknown aggregation %d", agg);
+  if (g->butterfly_agg == PB_BFLY_SORT && agg != PB_AGG_SORT)
+    return fail(PB_ERR_INVALID, "butterfly re-aggregation by sorting needs wedge aggregation PB_AGG_SORT");
   const uint64_t n = g->n, na = 2 * g->m;
   const bool want_pv = o.U || o.V, want_pe = o.E != nullptr;
   uint64_t budget = scratch_bytes ? scratch_bytes : (uint64_t(16) << 30);
@@ -1336,10 +1474,17 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     pb_status st;
     if (agg == PB_AGG_SORT) {
       PhaseScope ph(PB_PHASE_SORT, s);
-      if (want_pv && want_pe) st = run_sort<true, true>(g, a, budget, p.owner_lo, p.owner_hi, s);
-      else if (want_pv) st = run_sort<true, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
-      else if (want_pe) st = run_sort<false, true>(g, a, budget, p.owner_lo, p.owner_hi, s);
-      else st = run_sort<false, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      const bool re = g->butterfly_agg == PB_BFLY_SORT;
+      if (want_pv && want_pe)
+        st = re ? run_sort<true, true, true>(g, a, budget, p.owner_lo, p.owner_hi, s)
+                : run_sort<true, true, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      else if (want_pv)
+        st = re ? run_sort<true, false, true>(g, a, budget, p.owner_lo, p.owner_hi, s)
+                : run_sort<true, false, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      else if (want_pe)
+        st = re ? run_sort<false, true, true>(g, a, budget, p.owner_lo, p.owner_hi, s)
+                : run_sort<false, true, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
+      else st = run_sort<false, false, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
       if (st == PB_OK) ph.finish(s, g->W);
     } else if (want_pv && want_pe) st = run_tiers<true, true>(g, a, p, budget, s);
     else if (want_pv) st = run_tiers<true, false>(g, a, p, budget, s);

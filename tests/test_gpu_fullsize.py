@@ -72,6 +72,19 @@ def test_cl2_every_aggregation_and_retrieval(pb, cl2, kind):
     G.free()
 
 
+def test_cl2_sort_reaggregation_matches_oracle(pb, cl2):
+    g, ref = cl2
+    G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree").set_butterfly_aggregation("sort")
+    for rt in ["low", "high"]:
+        G.set_retrieval(rt)
+        c = G.count_all("sort")
+        assert c.global_count == ref.global_count, rt
+        np.testing.assert_array_equal(c.per_vertex_U, ref.per_vertex[: g.nU])
+        np.testing.assert_array_equal(c.per_vertex_V, ref.per_vertex[g.nU:])
+        np.testing.assert_array_equal(c.per_edge, ref.per_edge)
+    G.free()
+
+
 def test_cl3_batch_16gib_invariants_and_samples(pb):
     g = synth.workload(3)
     G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
