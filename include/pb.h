@@ -141,7 +141,10 @@ typedef struct {
  * pairs collapse into one edge; per-edge outputs still have one entry per
  * input pair, in input order.  Returns PB_ERR_INVALID if u[k] >= nU or
  * v[k] >= nV for any k.  The graph is ranked with PB_RANK_SIDE until pb_rank
- * is called.  *out receives the handle (NULL on failure). */
+ * is called; that ranking is computed on the first call that needs one (a
+ * count, pb_wedge_count, pb_graph_info, ...), so pb_rank straight after this
+ * call runs PREPROCESS once.  Calls without a stream argument that trigger it
+ * use the legacy default stream.  *out receives the handle (NULL on failure). */
 pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u,
                               const uint32_t *v, int on_device, void *stream,
                               pb_graph **out);

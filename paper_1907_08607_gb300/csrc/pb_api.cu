@@ -176,6 +176,15 @@ struct DeviceGuard {
   }
 };
 
+pb_status ensure_ranked(const pb_graph *cg, cudaStream_t s) {
+  pb_graph *g = const_cast<pb_graph *>(cg);  // ranking on first use does not change what the graph is
+  if (g->rank_kind >= 0) return PB_OK;
+  DeviceGuard dg(g->device);
+  PhaseScope ph(PB_PHASE_RANK, s);
+  PB_TRY(rank_graph(g, PB_RANK_SIDE, nullptr, 0, s));
+  ph.finish(s);
+  return PB_OK;
+}
 }  // namespace pb
 
 using namespace pb;
@@ -241,11 +250,8 @@ pb_status pb_graph_from_edges(uint32_t nU, uint32_t nV, uint64_t m, const uint32
     st = build_graph(g, u, v, on_device, s);
     if (st == PB_OK) ph.finish(s);
   }
-  if (st == PB_OK) {
-    PhaseScope ph(PB_PHASE_RANK, s);
-    st = rank_graph(g, PB_RANK_SIDE, nullptr, 0, s);
-    if (st == PB_OK) ph.finish(s);
-  }
+  // The side ranking is computed on first use (ensure_ranked), so that a
+  // pb_rank right after this call runs PREPROCESS once.
   cudaError_t e = cudaStreamSynchronize(s);
   prof_flush();
   if (st == PB_OK && e != cudaSuccess) st = cuda_fail(e, "graph build", __FILE__, __LINE__);
@@ -310,9 +316,9 @@ pb_status pb_set_butterfly_aggregation(pb_graph *g, pb_bfly_agg b) {
 pb_status pb_graph_ranks(const pb_graph *g, uint32_t *rank_of, int out_on_device, void *stream) {
   clear_error();
   if (!g || !rank_of) return fail(PB_ERR_INVALID, "graph or rank_of is NULL");
-  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
   DeviceGuard dg(g->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PB_TRY(ensure_ranked(g, s));
   PB_CUDA(cudaMemcpyAsync(rank_of, g->rank, g->n * sizeof(uint32_t),
                           out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   PB_CUDA(cudaStreamSynchronize(s));
@@ -359,9 +365,9 @@ pb_status pb_count_owner_range(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, 
 pb_status pb_wedge_prefix(const pb_graph *g, uint64_t *out, int out_on_device, void *stream) {
   clear_error();
   if (!g || !out) return fail(PB_ERR_INVALID, "graph or out is NULL");
-  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
   DeviceGuard dg(g->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PB_TRY(ensure_ranked(g, s));
   const uint64_t *src = g->retrieval == PB_RETRIEVE_LOW ? g->wpre : g->wpre_rev;
   PB_CUDA(cudaMemcpyAsync(out, src, (g->n + 1) * sizeof(uint64_t),
                           out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -389,7 +395,8 @@ pb_status pb_count_edge(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, uint64_
 pb_status pb_wedge_count(const pb_graph *g, uint64_t *W) {
   clear_error();
   if (!g || !W) return fail(PB_ERR_INVALID, "graph or W is NULL");
-  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
+  PB_TRY(ensure_ranked(g, nullptr));
+  PB_CUDA(cudaStreamSynchronize(nullptr));
   *W = g->W;
   return PB_OK;
 }
@@ -397,6 +404,8 @@ pb_status pb_wedge_count(const pb_graph *g, uint64_t *W) {
 pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info) {
   clear_error();
   if (!g || !info) return fail(PB_ERR_INVALID, "graph or info is NULL");
+  PB_TRY(ensure_ranked(g, nullptr));
+  PB_CUDA(cudaStreamSynchronize(nullptr));
   info->nU = g->nU;
   info->nV = g->nV;
   info->m_in = g->m_in;

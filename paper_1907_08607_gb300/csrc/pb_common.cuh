@@ -146,6 +146,8 @@ pb_status build_graph(pb_graph *g, const uint32_t *u, const uint32_t *v, int on_
 pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_device,
                      cudaStream_t s);
 void free_ranked(pb_graph *g, cudaStream_t s);
+// Ranks g by side order if it has no ranking yet (pb_api.cu); asynchronous on s.
+pb_status ensure_ranked(const pb_graph *g, cudaStream_t s);
 struct CountOut {
   uint64_t *global = nullptr;  // host
   uint64_t *U = nullptr, *V = nullptr, *E = nullptr;

@@ -64,7 +64,10 @@ constexpr int LW_WARPS = LW_THREADS / 32;
 constexpr int LW_CAP = 1024;          // per-warp table entries (>= 2 * LIGHT_MAX)
 constexpr uint32_t MED_MAX = 4096;
 constexpr int MB_THREADS = 512;
+constexpr int MB_WARPS = MB_THREADS / 32;
 constexpr int MB_CAP = 8192;          // per-block table entries (>= 2 * MED_MAX)
+// medium-tier dynamic shared memory: keys, 16-bit counts, 16-bit table position per wedge
+constexpr size_t MB_SMEM = (MB_CAP + MB_CAP / 2) * sizeof(uint32_t) + MED_MAX * sizeof(uint16_t);
 constexpr int HB_THREADS = 1024;
 
 __device__ __forceinline__ void add_global(unsigned long long *acc, unsigned long long v) {
@@ -185,12 +188,12 @@ __device__ __forceinline__ uint32_t owner_span(const CArgs &a, uint32_t x) {
 // The same table with 16-bit counts, two per 32-bit word (cnt16 holds cap/2
 // words).  Only for owners whose wedge count, and so every group size d, is
 // below 2^16: the light tier.
-__device__ __forceinline__ void sh_add16(uint32_t *key, uint32_t *cnt16, int lg, uint32_t x,
-                                         unsigned long long *err) {
+__device__ __forceinline__ uint32_t sh_add16(uint32_t *key, uint32_t *cnt16, int lg, uint32_t x,
+                                             unsigned long long *err) {
   const uint32_t mask = (1u << lg) - 1;
   uint32_t h = hash_home(x, lg);
   for (uint32_t probe = 0;; probe++) {
-    if (probe > mask) { atomicOr(err, 1ull); return; }
+    if (probe > mask) { atomicOr(err, 1ull); return 0; }
     uint32_t k = reinterpret_cast<volatile uint32_t *>(key)[h];
     if (k == x) break;
     if (k == EMPTY) {
@@ -200,6 +203,7 @@ __device__ __forceinline__ void sh_add16(uint32_t *key, uint32_t *cnt16, int lg,
     h = (h + 1) & mask;
   }
   atomicAdd(&cnt16[h >> 1], 1u << ((h & 1u) << 4));
+  return h;
 }
 
 __device__ __forceinline__ uint32_t cnt16_at(const uint32_t *cnt16, uint32_t h) {
@@ -267,7 +271,7 @@ __device__ __forceinline__ void warp_run_add(unsigned long long *acc, uint32_t k
 constexpr int LW_BATCH = 4;
 
 template <bool PV, bool PE, bool MULTI>
-__global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *__restrict__ list,
+__global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_t *__restrict__ list,
                                                       uint32_t nlist, const uint64_t *__restrict__ items,
                                                       const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP / 2 count words
@@ -299,12 +303,16 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *
     for (uint32_t t = lane; t < cap / 2; t += 32) cnt[t] = 0;
     __syncwarp();
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
+    // An owner with at most 32 neighbours has one chunk: its neighbour data
+    // stay in registers for the second pass.
+    uint32_t ky = 0, kc = 0, koy = 0, kincl = 0;
     for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
       const uint32_t i = k0 + lane;
       const bool v = i < dp;
       uint32_t y, c, oy;
       owner_nbr(a, base, i, v, y, c, oy);
       const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
+      ky = y; kc = c; koy = oy; kincl = incl;
       for (uint32_t wb = 0; wb < tot; wb += LW_BATCH * 32) {
         uint32_t x2v[LW_BATCH];
 #pragma unroll
@@ -339,9 +347,12 @@ __global__ void __launch_bounds__(LW_THREADS) k_light(CArgs a0, const uint32_t *
       for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
         const uint32_t i = k0 + lane;
         const bool v = i < dp;
-        uint32_t y, c, oy;
-        owner_nbr(a, base, i, v, y, c, oy);
-        const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
+        uint32_t y = ky, c = kc, oy = koy, incl = kincl;
+        if (dp > 32) {
+          owner_nbr(a, base, i, v, y, c, oy);
+          incl = warp_incl_scan(c);
+        }
+        const uint32_t tot = __shfl_sync(FULL, incl, 31);
         for (uint32_t wb = 0; wb < tot; wb += LW_BATCH * 32) {
           uint32_t x2v[LW_BATCH], srcv[LW_BATCH], slv[LW_BATCH], dv[LW_BATCH];
 #pragma unroll
@@ -391,21 +402,43 @@ __device__ __forceinline__ uint32_t block_find(const uint32_t *s_incl, uint32_t 
   return lo;
 }
 
-// Medium tier: one block per first endpoint, table in (dynamic) shared memory.
+// Medium tier: one block per owner, table in (dynamic) shared memory.  Up to
+// MB_THREADS neighbours of the owner are loaded at once (one per thread) and
+// flattened 32 at a time with warp scans into shared memory; the wedges of
+// each 32-neighbour chunk are then dealt out to all warps (wedge wi to thread
+// wi mod MB_THREADS), each located with the shuffle search of the light tier,
+// MB_BATCH wedges in flight per thread.  With per-vertex or per-edge outputs
+// the first pass records each wedge's table position, so the second pass
+// reads its group size directly, and an owner with at most MB_THREADS
+// neighbours keeps its flattening for the second pass.
+constexpr int MB_BATCH = 4;
+
+// Chunk ch of the staged neighbours as seen by one lane: inclusive wedge
+// count, wedge count and first slot of the lane's neighbour.
+__device__ __forceinline__ void mb_chunk(const uint32_t *s_incl, const uint32_t *s_oy, uint32_t ch, uint32_t lane,
+                                         uint32_t &incl, uint32_t &c, uint32_t &oy) {
+  incl = s_incl[ch * 32 + lane];
+  const uint32_t prev = __shfl_up_sync(FULL, incl, 1);
+  c = lane ? incl - prev : incl;
+  oy = s_oy[ch * 32 + lane];
+}
+
 template <bool PV, bool PE, bool MULTI>
-__global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t *__restrict__ list,
+__global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32_t *__restrict__ list,
                                                        uint32_t nlist, const uint64_t *__restrict__ items,
                                                        const CArgs *__restrict__ tab) {
-  extern __shared__ uint32_t dsm[];  // MB_CAP keys, then MB_CAP / 2 words of 16-bit counts
+  // MB_CAP keys, MB_CAP / 2 words of 16-bit counts, then MED_MAX 16-bit table positions
+  extern __shared__ uint32_t dsm[];
   uint32_t *key = dsm, *cnt = dsm + MB_CAP;
+  uint16_t *pos = reinterpret_cast<uint16_t *>(dsm + MB_CAP + MB_CAP / 2);
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
-  __shared__ uint32_t s_incl[MB_THREADS], s_ex[MB_THREADS], s_oy[MB_THREADS];
+  __shared__ uint32_t s_incl[MB_THREADS], s_oy[MB_THREADS];  // per 32-chunk inclusive counts, first slots
   __shared__ unsigned long long s_sum[MB_THREADS];
-  __shared__ uint32_t s_w[33];
   __shared__ unsigned long long s_w64[33];
   __shared__ uint32_t s_item;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   if (s_hub) hub_zero(s_hub);
@@ -425,26 +458,53 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
       x1 = list[it];
     }
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
+    if (wc > MED_MAX) {  // the tier split guarantees wc <= MED_MAX
+      if (tid == 0) atomicOr(err, 16ull);
+      __syncthreads();
+      continue;
+    }
     const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t cap = 1u << lg;
     for (uint32_t t = tid; t < cap; t += MB_THREADS) key[t] = EMPTY;
     for (uint32_t t = tid; t < cap / 2; t += MB_THREADS) cnt[t] = 0;
-    __syncthreads();
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
-    for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
-      const uint32_t i = k0 + tid;
-      const bool v = i < dp;
-      uint32_t y, c, oy;
-      owner_nbr(a, base, i, v, y, c, oy);
-      uint32_t tot;
-      const uint32_t incl = block_incl_scan(c, s_w, &tot);
-      s_incl[tid] = incl;
-      s_ex[tid] = incl - c;
-      s_oy[tid] = oy;
-      __syncthreads();
-      for (uint32_t wi = tid; wi < tot; wi += MB_THREADS) {
-        uint32_t src = block_find(s_incl, MB_THREADS, wi);
-        sh_add16(key, cnt, lg, a.adj[s_oy[src] + (wi - s_ex[src])], &a.acc[ACC_ERR]);
+    uint32_t my_y = 0;  // this thread's neighbour in the current group of MB_THREADS
+    uint32_t done = 0;  // wedges of the chunks before the current one
+    for (uint32_t s0 = 0; s0 < dp; s0 += MB_THREADS) {
+      {
+        uint32_t c, oy;
+        owner_nbr(a, base, s0 + tid, s0 + tid < dp, my_y, c, oy);
+        s_incl[tid] = warp_incl_scan(c);
+        s_oy[tid] = oy;
+      }
+      __syncthreads();  // also orders the table reset before the first insert
+      const uint32_t left = dp - s0, nch = left >= MB_THREADS ? MB_WARPS : (left + 31) / 32;
+      for (uint32_t ch = 0; ch < nch; ch++) {
+        uint32_t incl, c, oy;
+        mb_chunk(s_incl, s_oy, ch, lane, incl, c, oy);
+        const uint32_t tot = __shfl_sync(FULL, incl, 31);
+        for (uint32_t wb = 0; wb < tot; wb += MB_BATCH * MB_THREADS) {
+          uint32_t x2v[MB_BATCH];
+#pragma unroll
+          for (int q = 0; q < MB_BATCH; q++) {
+            const uint32_t wi = wb + q * MB_THREADS + tid;
+            x2v[q] = 0;
+            if (wb + q * MB_THREADS + w * 32 < tot) {  // warp-uniform
+              uint32_t src, slot;
+              warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
+              if (wi < tot) x2v[q] = a.adj[slot];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < MB_BATCH; q++) {
+            const uint32_t wi = wb + q * MB_THREADS + tid;
+            if (wi < tot) {
+              const uint32_t h = sh_add16(key, cnt, lg, x2v[q], err);
+              if (PV || PE) pos[done + wi] = static_cast<uint16_t>(h);
+            }
+          }
+        }
+        done += tot;
       }
       __syncthreads();
     }
@@ -464,38 +524,47 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
       if (PV && own) atomicAdd(&a.pv[x1], own);
     }
     if (PV || PE) {
-      for (uint32_t k0 = 0; k0 < dp; k0 += MB_THREADS) {
-        const uint32_t i = k0 + tid;
-        const bool v = i < dp;
-        uint32_t y, c, oy;
-        owner_nbr(a, base, i, v, y, c, oy);
-        uint32_t tot;
-        const uint32_t incl = block_incl_scan(c, s_w, &tot);
-        s_incl[tid] = incl;
-        s_ex[tid] = incl - c;
-        s_oy[tid] = oy;
-        __syncthreads();
-        for (uint32_t wb = 0; wb < tot; wb += MB_THREADS) {
-          const uint32_t wi = wb + tid;
-          uint32_t src = 0;
-          unsigned long long t = 0;
-          if (wi < tot) {
-            src = block_find(s_incl, MB_THREADS, wi);
-            uint32_t slot = s_oy[src] + (wi - s_ex[src]);
-            uint32_t d = sh_get16(key, cnt, lg, a.adj[slot], &a.acc[ACC_ERR]);
-            if (d > 1) {
-              t = d - 1;
-              if (PE) atomicAdd(&a.es[slot], t);
+      done = 0;
+      for (uint32_t s0 = 0; s0 < dp; s0 += MB_THREADS) {
+        if (dp > MB_THREADS) {  // otherwise the first pass's flattening is still in place
+          uint32_t c, oy;
+          owner_nbr(a, base, s0 + tid, s0 + tid < dp, my_y, c, oy);
+          s_incl[tid] = warp_incl_scan(c);
+          s_oy[tid] = oy;
+          __syncthreads();
+        }
+        const uint32_t left = dp - s0, nch = left >= MB_THREADS ? MB_WARPS : (left + 31) / 32;
+        for (uint32_t ch = 0; ch < nch; ch++) {
+          uint32_t incl, c, oy;
+          mb_chunk(s_incl, s_oy, ch, lane, incl, c, oy);
+          const uint32_t tot = __shfl_sync(FULL, incl, 31);
+          for (uint32_t wb = 0; wb < tot; wb += MB_BATCH * MB_THREADS) {
+#pragma unroll
+            for (int q = 0; q < MB_BATCH; q++) {
+              const uint32_t wi = wb + q * MB_THREADS + tid;
+              if (wb + q * MB_THREADS + w * 32 < tot) {  // warp-uniform
+                uint32_t src, slot;
+                warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
+                unsigned long long t = 0;
+                if (wi < tot) {
+                  const uint32_t d = cnt16_at(cnt, pos[done + wi]);
+                  if (d > 1) {
+                    t = d - 1;
+                    if (PE) atomicAdd(&a.es[slot], t);
+                  }
+                }
+                warp_run_add(s_sum + ch * 32, src, t);
+              }
             }
           }
-          warp_run_add(s_sum, src, t);
+          done += tot;
         }
         __syncthreads();
-        if (v) {
+        if (s0 + tid < dp) {
           unsigned long long sm = s_sum[tid];
           if (sm) {
-            if (PV) pv_add(s_hub, a, y, sm);
-            if (PE) atomicAdd(&a.es[base + i], sm);
+            if (PV) pv_add(s_hub, a, my_y, sm);
+            if (PE) atomicAdd(&a.es[base + s0 + tid], sm);
             s_sum[tid] = 0;
           }
         }
@@ -520,6 +589,10 @@ __global__ void __launch_bounds__(MB_THREADS) k_medium(CArgs a0, const uint32_t 
 // first endpoint per block and its own dense array.
 // Dense slots are indexed by the second endpoint's offset within its side.
 constexpr int HB_BATCH = 4;
+// Shared-memory histogram of the first labels of a side: with the cache
+// optimisation the second endpoints are the lower-ranked ones, so nearly all
+// of a heavy owner's wedges land there (the highest-degree vertices).
+constexpr uint32_t HB_HOT = 16384;
 
 struct HeavySlots {
   uint32_t *A;        // dense: [nslots][side] counts (all zero between uses)
@@ -529,6 +602,7 @@ struct HeavySlots {
   uint32_t *tcnt;     // [nslots][2] touched counters (alternating)
   uint32_t *item;     // [nslots] current work item of the slot
   uint64_t side, tcap, hcap;
+  uint32_t hot;       // dense, one block per slot: labels [0, hot) of the side counted in shared memory
 };
 
 // Appends second endpoints seen for the first time to the touched list
@@ -583,9 +657,13 @@ __device__ __forceinline__ void heavy_insert(const HeavySlots &h, uint32_t slot,
 }
 
 template <bool DENSE>
-__device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot, const uint32_t *A, int lg,
-                                              uint32_t x2, uint32_t base, unsigned long long *err) {
-  if (DENSE) return __ldcg(&A[x2 - base]);
+__device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot, const uint32_t *A,
+                                              const uint32_t *hot, int lg, uint32_t x2, uint32_t base,
+                                              unsigned long long *err) {
+  if (DENSE) {
+    const uint32_t r = x2 - base;
+    return r < h.hot ? hot[r] : __ldcg(&A[r]);
+  }
   const uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
   const uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
   const uint32_t mask = (1u << lg) - 1;
@@ -611,12 +689,15 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
   __shared__ unsigned long long s_w64[33];
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
+  extern __shared__ uint32_t hb_hot[];  // h.hot counts (dense, one block per slot)
   uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.side : nullptr;
   uint32_t *T = DENSE ? h.T + static_cast<size_t>(slot) * h.tcap : nullptr;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   if (s_hub) hub_zero(s_hub);
+  if (DENSE)
+    for (uint32_t t = tid; t < h.hot; t += HB_THREADS) hb_hot[t] = 0;  // ordered by the first cluster barrier
   for (uint32_t k = 0;; k++) {
     if (crank == 0 && tid == 0) h.item[slot] = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QHEAVY], 1ull));
     cl.sync();
@@ -669,8 +750,11 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
           // issue every atomic of the batch before any result is used
           uint32_t old[HB_BATCH];
 #pragma unroll
-          for (int q = 0; q < HB_BATCH; q++)
-            old[q] = wb + q * HB_THREADS + tid < hi ? atomicAdd(&A[x2v[q] - base], 1u) : 1u;
+          for (int q = 0; q < HB_BATCH; q++) {
+            const uint32_t r = x2v[q] - base;
+            old[q] = wb + q * HB_THREADS + tid < hi ? (r < h.hot ? atomicAdd(&hb_hot[r], 1u) : atomicAdd(&A[r], 1u))
+                                                    : 1u;
+          }
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++) dense_touch(h, T, tc, x2v[q], old[q] == 0u, err);
         } else {
@@ -688,7 +772,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
       const uint32_t nt = __ldcg(tc);
       for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) {
         uint32_t x2 = __ldcg(&T[t]);
-        unsigned long long d = __ldcg(&A[x2 - base]), b = d * (d - 1) / 2;
+        const uint32_t r = x2 - base;
+        unsigned long long d = r < h.hot ? hb_hot[r] : __ldcg(&A[r]), b = d * (d - 1) / 2;
         own += b;
         if (PV && b) pv_add(s_hub, a, x2, b);
       }
@@ -742,7 +827,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
           }
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++)
-            dv[q] = wb + q * HB_THREADS + tid < hi ? heavy_get<DENSE>(h, slot, A, lg, x2v[q], base, err) : 0;
+            dv[q] = wb + q * HB_THREADS + tid < hi ? heavy_get<DENSE>(h, slot, A, hb_hot, lg, x2v[q], base, err) : 0;
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++) {
             unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
@@ -766,7 +851,11 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
     // ---- restore the slot to all-zero / all-empty
     if (DENSE) {
       const uint32_t nt = __ldcg(tc);
-      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) A[__ldcg(&T[t]) - base] = 0;
+      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) {
+        const uint32_t r = __ldcg(&T[t]) - base;
+        if (r < h.hot) hb_hot[r] = 0;
+        else A[r] = 0;
+      }
     } else {
       uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
       uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
@@ -1063,12 +1152,12 @@ __global__ void k_out_edge(const unsigned long long *__restrict__ es, const uint
 // Host orchestration.
 
 template <class K, class... Args>
-static pb_status launch_cluster(K kernel, unsigned grid, unsigned block, unsigned cl, cudaStream_t s,
+static pb_status launch_cluster(K kernel, unsigned grid, unsigned block, unsigned cl, size_t smem, cudaStream_t s,
                                 Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1083,10 +1172,11 @@ static pb_status launch_cluster(K kernel, unsigned grid, unsigned block, unsigne
 }
 
 template <class K>
-static int max_clusters(K kernel, unsigned block, unsigned cl) {
+static int max_clusters(K kernel, unsigned block, unsigned cl, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl * 256);
   cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cl;
@@ -1159,7 +1249,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
     }
     if (nm) {
       PhaseScope ph(PB_PHASE_MEDIUM, s);
-      const size_t smem = (MB_CAP + MB_CAP / 2) * sizeof(uint32_t);
+      const size_t smem = MB_SMEM;
       PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE, false>, MB_THREADS, smem);
@@ -1220,7 +1310,13 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         if (pt.cnt == 0) continue;
         const unsigned cl = pt.cl;
         if (cl > 8) PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        int nc = max_clusters(kern, HB_THREADS, cl);
+        // A slot processed by one block keeps the counts of the first HB_HOT
+        // labels of the side in shared memory (dense mode).
+        const uint32_t hot = (p.dense && cl == 1) ? HB_HOT : 0;
+        const size_t hsmem = hot * sizeof(uint32_t);
+        if (hsmem) PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+        hs.hot = hot;
+        int nc = max_clusters(kern, HB_THREADS, cl, hsmem);
         if (nc <= 0) nc = sms / static_cast<int>(cl);
         uint64_t nslots = static_cast<uint64_t>(nc);
         if (&pt == &parts[0] && p.max_slots && nslots > p.max_slots) nslots = p.max_slots;
@@ -1244,7 +1340,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         hs.item = hs.tcnt + 2 * nslots;
         if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-        if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, s, a, pt.list, pt.cnt,
+        if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list, pt.cnt,
                                  hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) break;
       }
       if (st != PB_OK) break;
@@ -1421,7 +1517,7 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
 }
 
 pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut &o, cudaStream_t s) {
-  if (g->rank_kind < 0) PB_TRY(rank_graph(g, PB_RANK_SIDE, nullptr, 0, s));
+  PB_TRY(ensure_ranked(g, s));
   if (agg < 0 || agg > PB_AGG_AUTO) return fail(PB_ERR_INVALID, "unknown aggregation %d", agg);
   if (g->butterfly_agg == PB_BFLY_SORT && agg != PB_AGG_SORT)
     return fail(PB_ERR_INVALID, "butterfly re-aggregation by sorting needs wedge aggregation PB_AGG_SORT");
@@ -1630,7 +1726,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
   PB_CUDA(cudaFuncSetAttribute(k_light<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t))));
   PB_CUDA(cudaFuncSetAttribute(k_medium<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)((MB_CAP + MB_CAP / 2) * sizeof(uint32_t))));
+                               (int)MB_SMEM));
   PB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   pb_status st = PB_OK;
   do {
@@ -1654,7 +1750,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch light launch", __FILE__, __LINE__); break; }
     }
     if (b->nm) {
-      const size_t smem = (MB_CAP + MB_CAP / 2) * sizeof(uint32_t);
+      const size_t smem = MB_SMEM;
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, false, true>, MB_THREADS, smem);
       unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
@@ -1666,7 +1762,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
     if (b->nh) {
       e1 = cudaMemsetAsync(b->scratch, 0, b->nslots * b->slot_bytes + b->nslots * 7 * sizeof(uint32_t) + 64, s);
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (slots)", __FILE__, __LINE__); break; }
-      if ((st = launch_cluster(k_heavy<PV, false, true, true>, static_cast<unsigned>(b->nslots), HB_THREADS, 1, s, a0,
+      if ((st = launch_cluster(k_heavy<PV, false, true, true>, static_cast<unsigned>(b->nslots), HB_THREADS, 1, 0, s, a0,
                                (const uint32_t *)nullptr, b->nh, b->hs, (const uint64_t *)b->heavy,
                                (const CArgs *)b->tab)) != PB_OK) break;
     }
@@ -1792,7 +1888,8 @@ extern "C" {
 pb_status pb_autotune(const pb_graph *g, pb_plan_t *plan) {
   clear_error();
   if (!g || !plan) return fail(PB_ERR_INVALID, "graph or plan is NULL");
-  if (g->rank_kind < 0) return fail(PB_ERR_INVALID, "graph is not ranked");
+  PB_TRY(ensure_ranked(g, nullptr));
+  PB_CUDA(cudaStreamSynchronize(nullptr));
   make_plan(g, plan);
   return PB_OK;
 }
@@ -1808,10 +1905,12 @@ pb_status pb_batch_create(pb_graph *const *graphs, uint32_t ng, int want_vertex,
   b->ng = ng;
   b->pv = want_vertex != 0;
   for (uint32_t i = 0; i < ng; i++) {
-    if (!graphs[i] || graphs[i]->rank_kind < 0 || graphs[i]->device != b->device) {
+    if (!graphs[i] || graphs[i]->device != b->device) {
       delete b;
-      return fail(PB_ERR_INVALID, "graph %u is NULL, not ranked, or on another device", i);
+      return fail(PB_ERR_INVALID, "graph %u is NULL or on another device", i);
     }
+    pb_status rs = ensure_ranked(graphs[i], static_cast<cudaStream_t>(stream));
+    if (rs != PB_OK) { delete b; return rs; }
     if (graphs[i]->n >= (uint64_t(1) << 32)) { delete b; return fail(PB_ERR_INVALID, "graph too large"); }
     b->graphs.push_back(graphs[i]);
   }

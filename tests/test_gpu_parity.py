@@ -185,6 +185,29 @@ def test_duplicates_and_device_inputs(pb, er1):
     G.free()
 
 
+def test_side_ranking_until_ranked(pb, er1):
+    """Before pb_rank the graph behaves as side-ranked (computed on first use):
+    every query and count sees the side order's wedges and exact counts; a
+    pb_rank straight after construction replaces it."""
+    g = er1
+    ref = oracle.count(g.nU, g.nV, g.u, g.v, kind="degree")
+    W_side = oracle.wedges(g.nU, g.nV, g.u, g.v, kind="side")
+    G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v)
+    inf = G.info()
+    assert inf.rank_kind == 0 and inf.W == W_side
+    np.testing.assert_array_equal(G.ranks(), oracle.rank(g.nU, g.nV, g.u, g.v, "side"))
+    _assert_same(G.count_all("hash"), ref, g.nU)
+    G.free()
+    G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v)
+    _assert_same(G.count_all("hist"), ref, g.nU)     # a count first
+    assert G.wedges == W_side
+    G.free()
+    G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
+    assert G.wedges == oracle.wedges(g.nU, g.nV, g.u, g.v, kind="degree")
+    _assert_same(G.count_all("auto"), ref, g.nU)
+    G.free()
+
+
 def test_degenerate_inputs(pb):
     e = np.zeros(0, np.uint32)
     G = pb.Graph.from_edges(3, 4, e, e)
