@@ -221,6 +221,8 @@ __device__ __forceinline__ uint32_t sh_get16(const uint32_t *key, const uint32_t
   return cnt16_at(cnt16, h);
 }
 
+// Table size: a power of two at least twice the bound on distinct second
+// endpoints (load factor at most 1/2).
 __device__ __forceinline__ int table_lg(uint64_t wc, uint64_t n, uint32_t nU, uint32_t x1, int rev) {
   uint64_t dmax = distinct_bound(wc, n, nU, x1, rev);
   int lg = 5;
@@ -263,6 +265,25 @@ __device__ __forceinline__ void warp_run_add(unsigned long long *acc, uint32_t k
     if (lane + o < 32 && (heads & (((1u << o) - 1u) << (lane + 1))) == 0) v += u;
   }
   if (head && v) atomicAdd(&acc[key], v);
+}
+
+// As warp_run_add, for v < 2^32: each run's lanes reduce over their own lane
+// mask (the 16-bit halves separately, so no partial sum overflows 32 bits).
+// Faster than the shuffle scan in the light tier, slower in the others.
+__device__ __forceinline__ void warp_run_add_rx(unsigned long long *acc, uint32_t key, unsigned long long v) {
+  const uint32_t lane = lane_id();
+  const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const uint32_t heads = __ballot_sync(FULL, head);
+  const uint32_t upto = 0xffffffffu >> (31 - lane);             // lanes 0..lane
+  const uint32_t start = 31 - __clz(heads & upto);               // this lane's run head
+  const uint32_t after = heads & ~upto;                          // heads beyond this lane
+  const uint32_t below_end = after ? (1u << (__ffs(after) - 1)) - 1u : 0xffffffffu;
+  const uint32_t run = below_end & ~((1u << start) - 1u);
+  const uint32_t v32 = static_cast<uint32_t>(v);
+  const uint32_t lo = __reduce_add_sync(run, v32 & 0xffffu), hi = __reduce_add_sync(run, v32 >> 16);
+  const unsigned long long sum = static_cast<unsigned long long>(lo) + (static_cast<unsigned long long>(hi) << 16);
+  if (head && sum) atomicAdd(&acc[key], sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,7 +389,7 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
           for (int q = 0; q < LW_BATCH; q++) {
             unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
             if (PE && t) atomicAdd(&a.es[slv[q]], t);
-            warp_run_add(s_sum[w], srcv[q], t);
+            warp_run_add_rx(s_sum[w], srcv[q], t);
           }
         }
         __syncwarp();
