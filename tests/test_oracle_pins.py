@@ -104,6 +104,20 @@ def test_oracle_matches_brute_force_on_tiny_graphs(tiny):
             assert oracle.wedges(g.nU, g.nV, g.u, g.v, rank_of=rk) == bw
 
 
+def test_oracle_matches_brute_force_on_1000_more_tiny_graphs():
+    """A thousand further seeded tiny graphs (ER and Chung-Lu, up to 31 x 31),
+    every ranking: global, per-vertex and per-edge counts equal the
+    definitions, and W equals the brute-force wedge count."""
+    for i, g in enumerate(tiny_graphs(1000, seed=0x51A8)):
+        glob, pv, pe = brute.counts(g.nU, g.nV, g.u, g.v)
+        for kind in RANKS:
+            c = oracle.count(g.nU, g.nV, g.u, g.v, kind=kind, nthreads=1)
+            assert c.global_count == glob, (g.name, kind)
+            np.testing.assert_array_equal(c.per_vertex.astype(np.int64), pv)
+            np.testing.assert_array_equal(c.per_edge.astype(np.int64), pe)
+            assert c.W == brute.wedges(g.nU, g.nV, g.u, g.v, oracle.rank(g.nU, g.nV, g.u, g.v, kind)), (g.name, kind)
+
+
 def test_eq1_direct_matches_brute(tiny):
     for g in tiny[:20]:
         _, pv, _ = brute.counts(g.nU, g.nV, g.u, g.v)
