@@ -206,6 +206,27 @@ __device__ __forceinline__ uint32_t sh_add16(uint32_t *key, uint32_t *cnt16, int
   return h;
 }
 
+// As sh_add16, returning the table position with bit 15 set for the first
+// insertion of x (its count was 0).  Tables of at most 2^15 entries.
+__device__ __forceinline__ uint32_t sh_add16f(uint32_t *key, uint32_t *cnt16, int lg, uint32_t x,
+                                              unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t h = hash_home(x, lg);
+  for (uint32_t probe = 0;; probe++) {
+    if (probe > mask) { atomicOr(err, 1ull); return 0; }
+    uint32_t k = reinterpret_cast<volatile uint32_t *>(key)[h];
+    if (k == x) break;
+    if (k == EMPTY) {
+      uint32_t prev = atomicCAS(&key[h], EMPTY, x);
+      if (prev == EMPTY || prev == x) break;
+    }
+    h = (h + 1) & mask;
+  }
+  const uint32_t sh = (h & 1u) << 4;
+  const uint32_t old = atomicAdd(&cnt16[h >> 1], 1u << sh);
+  return h | (((old >> sh) & 0xffffu) == 0 ? 0x8000u : 0u);
+}
+
 __device__ __forceinline__ uint32_t cnt16_at(const uint32_t *cnt16, uint32_t h) {
   return (cnt16[h >> 1] >> ((h & 1u) << 4)) & 0xffffu;
 }
@@ -431,8 +452,14 @@ __device__ __forceinline__ uint32_t block_find(const uint32_t *s_incl, uint32_t 
 // MB_BATCH wedges in flight per thread.  With per-vertex or per-edge outputs
 // the first pass records each wedge's table position, so the second pass
 // reads its group size directly, and an owner with at most MB_THREADS
-// neighbours keeps its flattening for the second pass.
+// neighbours keeps its flattening for the second pass.  The table always has
+// MB_CAP entries and is cleared once per block: the endpoint phase and the
+// reset visit only the entries the owner used (the wedges that inserted a new
+// key are flagged in the recorded positions), so per-owner work scales with
+// its wedges, not with the table.
 constexpr int MB_BATCH = 4;
+constexpr int MB_LG = 13;
+static_assert((1 << MB_LG) == MB_CAP, "medium table size");
 
 // Chunk ch of the staged neighbours as seen by one lane: inclusive wedge
 // count, wedge count and first slot of the lane's neighbour.
@@ -463,6 +490,8 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   if (s_hub) hub_zero(s_hub);
+  for (uint32_t t = tid; t < MB_CAP; t += MB_THREADS) key[t] = EMPTY;
+  for (uint32_t t = tid; t < MB_CAP / 2; t += MB_THREADS) cnt[t] = 0;
   for (;;) {
     if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
     __syncthreads();
@@ -484,10 +513,6 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
       __syncthreads();
       continue;
     }
-    const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
-    const uint32_t cap = 1u << lg;
-    for (uint32_t t = tid; t < cap; t += MB_THREADS) key[t] = EMPTY;
-    for (uint32_t t = tid; t < cap / 2; t += MB_THREADS) cnt[t] = 0;
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     uint32_t my_y = 0;  // this thread's neighbour in the current group of MB_THREADS
     uint32_t done = 0;  // wedges of the chunks before the current one
@@ -519,23 +544,22 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
 #pragma unroll
           for (int q = 0; q < MB_BATCH; q++) {
             const uint32_t wi = wb + q * MB_THREADS + tid;
-            if (wi < tot) {
-              const uint32_t h = sh_add16(key, cnt, lg, x2v[q], err);
-              if (PV || PE) pos[done + wi] = static_cast<uint16_t>(h);
-            }
+            if (wi < tot) pos[done + wi] = static_cast<uint16_t>(sh_add16f(key, cnt, MB_LG, x2v[q], err));
           }
         }
         done += tot;
       }
       __syncthreads();
     }
+    const uint32_t nw = done;  // the owner's wedges
     unsigned long long own = 0;
-    for (uint32_t t = tid; t < cap; t += MB_THREADS) {
-      uint32_t k = key[t];
-      if (k != EMPTY) {
-        unsigned long long d = cnt16_at(cnt, t), b = d * (d - 1) / 2;
+    for (uint32_t j = tid; j < nw; j += MB_THREADS) {
+      const uint32_t p = pos[j];
+      if (p & 0x8000u) {  // one flagged wedge per distinct second endpoint
+        const uint32_t h = p & 0x7fffu;
+        unsigned long long d = cnt16_at(cnt, h), b = d * (d - 1) / 2;
         own += b;
-        if (PV && b) pv_add(s_hub, a, k, b);
+        if (PV && b) pv_add(s_hub, a, key[h], b);
       }
     }
     own = block_sum(own, s_w64);
@@ -568,7 +592,7 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
                 warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
                 unsigned long long t = 0;
                 if (wi < tot) {
-                  const uint32_t d = cnt16_at(cnt, pos[done + wi]);
+                  const uint32_t d = cnt16_at(cnt, pos[done + wi] & 0x7fffu);
                   if (d > 1) {
                     t = d - 1;
                     if (PE) atomicAdd(&a.es[slot], t);
@@ -590,6 +614,16 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
           }
         }
         __syncthreads();
+      }
+    }
+    __syncthreads();
+    // reset the entries this owner used
+    for (uint32_t j = tid; j < nw; j += MB_THREADS) {
+      const uint32_t p = pos[j];
+      if (p & 0x8000u) {
+        const uint32_t h = p & 0x7fffu;
+        key[h] = EMPTY;
+        atomicAnd(&cnt[h >> 1], (h & 1u) ? 0x0000ffffu : 0xffff0000u);
       }
     }
     __syncthreads();
