@@ -927,6 +927,147 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
 }
 
 // ---------------------------------------------------------------------------
+// Heavy tier, one block per owner with a dense slot (no cluster): the owner's
+// neighbours are staged HB_THREADS at a time, and each warp takes whole
+// neighbours from a shared counter and walks the neighbour's segment of
+// second endpoints with its lanes (coalesced adjacency reads).  Counts of the
+// first h.hot labels of the side live in shared memory, the rest in the
+// slot's device-memory histogram; a touched list (device memory, counter in
+// shared memory) records each distinct second endpoint once.  The second
+// pass sums d - 1 over a segment in registers and adds it to the centre once.
+template <bool PV, bool PE>
+__global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *__restrict__ list, uint32_t nlist,
+                                                       HeavySlots h) {
+  extern __shared__ uint32_t hb_hot[];
+  __shared__ uint32_t s_c[HB_THREADS], s_oy[HB_THREADS], s_y[HB_THREADS];
+  __shared__ unsigned long long s_w64[33];
+  __shared__ unsigned long long s_hubarr[2 * HUBK];
+  __shared__ uint32_t s_item, s_next, s_nt;
+  unsigned long long *s_hub = PV ? s_hubarr : nullptr;
+  const uint32_t slot = blockIdx.x, tid = threadIdx.x, lane = lane_id();
+  uint32_t *A = h.A + static_cast<size_t>(slot) * h.side;
+  uint32_t *T = h.T + static_cast<size_t>(slot) * h.tcap;
+  unsigned long long *err = &a.acc[ACC_ERR];
+  unsigned long long gacc = 0;
+  if (s_hub) hub_zero(s_hub);
+  for (uint32_t t = tid; t < h.hot; t += HB_THREADS) hb_hot[t] = 0;
+  if (tid == 0) s_nt = 0;
+  for (;;) {
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QHEAVY], 1ull));
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= nlist) break;
+    const uint32_t x1 = list[it];
+    const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
+    const uint32_t xbase = a.off[x1], dp = owner_span(a, x1);
+    // ---- aggregate
+    for (uint32_t s0 = 0; s0 < dp; s0 += HB_THREADS) {
+      {
+        uint32_t y, c, oy;
+        owner_nbr(a, xbase, s0 + tid, s0 + tid < dp, y, c, oy);
+        s_c[tid] = c;
+        s_oy[tid] = oy;
+        s_y[tid] = y;
+      }
+      if (tid == 0) s_next = 0;
+      __syncthreads();
+      const uint32_t nn = dp - s0 < HB_THREADS ? dp - s0 : HB_THREADS;
+      for (;;) {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(&s_next, 1u);
+        j = __shfl_sync(FULL, j, 0);
+        if (j >= nn) break;
+        const uint32_t c = s_c[j], oy = s_oy[j];
+        for (uint32_t e0 = 0; e0 < c; e0 += 32) {
+          const bool act = e0 + lane < c;
+          uint32_t x2 = 0;
+          bool isnew = false;
+          if (act) {
+            x2 = a.adj[oy + e0 + lane];
+            const uint32_t r = x2 - base;
+            isnew = (r < h.hot ? atomicAdd(&hb_hot[r], 1u) : atomicAdd(&A[r], 1u)) == 0u;
+          }
+          const uint32_t bm = __ballot_sync(FULL, isnew);
+          if (bm) {
+            uint32_t b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&s_nt, static_cast<uint32_t>(__popc(bm)));
+            b0 = __shfl_sync(FULL, b0, 0);
+            if (isnew) {
+              const uint32_t at = b0 + __popc(bm & lanemask_lt());
+              if (at < h.tcap) T[at] = x2;
+              else atomicOr(err, 16ull);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const uint32_t nt = s_nt < h.tcap ? s_nt : static_cast<uint32_t>(h.tcap);
+    // ---- endpoints: C(d, 2) per distinct second endpoint
+    unsigned long long own = 0;
+    for (uint32_t t = tid; t < nt; t += HB_THREADS) {
+      const uint32_t x2 = T[t], r = x2 - base;
+      unsigned long long d = r < h.hot ? hb_hot[r] : __ldcg(&A[r]), b = d * (d - 1) / 2;
+      own += b;
+      if (PV && b) pv_add(s_hub, a, x2, b);
+    }
+    own = block_sum(own, s_w64);
+    if (tid == 0) {
+      gacc += own;
+      if (PV && own) atomicAdd(&a.pv[x1], own);
+    }
+    // ---- centres and edges: d - 1 per wedge
+    if (PV || PE) {
+      for (uint32_t s0 = 0; s0 < dp; s0 += HB_THREADS) {
+        if (dp > HB_THREADS) {  // otherwise the first pass's staging is still in place
+          uint32_t y, c, oy;
+          owner_nbr(a, xbase, s0 + tid, s0 + tid < dp, y, c, oy);
+          s_c[tid] = c;
+          s_oy[tid] = oy;
+          s_y[tid] = y;
+        }
+        if (tid == 0) s_next = 0;
+        __syncthreads();
+        const uint32_t nn = dp - s0 < HB_THREADS ? dp - s0 : HB_THREADS;
+        for (;;) {
+          uint32_t j = 0;
+          if (lane == 0) j = atomicAdd(&s_next, 1u);
+          j = __shfl_sync(FULL, j, 0);
+          if (j >= nn) break;
+          const uint32_t c = s_c[j], oy = s_oy[j];
+          unsigned long long sum = 0;
+          for (uint32_t e = lane; e < c; e += 32) {
+            const uint32_t sl = oy + e, r = a.adj[sl] - base;
+            const uint32_t d = r < h.hot ? hb_hot[r] : __ldcg(&A[r]);
+            if (d > 1) {
+              sum += d - 1;
+              if (PE) atomicAdd(&a.es[sl], static_cast<unsigned long long>(d - 1));
+            }
+          }
+          sum = warp_sum(sum);
+          if (lane == 0 && sum) {
+            if (PV) pv_add(s_hub, a, s_y[j], sum);
+            if (PE) atomicAdd(&a.es[xbase + s0 + j], sum);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // ---- reset the slot's used entries
+    for (uint32_t t = tid; t < nt; t += HB_THREADS) {
+      const uint32_t r = T[t] - base;
+      if (r < h.hot) hb_hot[r] = 0;
+      else A[r] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) s_nt = 0;
+  }
+  if (tid == 0) add_global(a.acc, gacc);
+  __syncthreads();
+  if (s_hub) hub_flush(s_hub, a);
+}
+
+// ---------------------------------------------------------------------------
 // Sort aggregation: the wedges of a chunk of first endpoints [lo, hi) are
 // materialised as keys ((x1 - lo) << bitsN) | x2, radix-sorted, and grouped;
 // a group's length is d(x1, x2).  The chunk is sized so that its wedges fit
@@ -1367,11 +1508,19 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         if (cl > 8) PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         // A slot processed by one block keeps the counts of the first HB_HOT
         // labels of the side in shared memory (dense mode).
-        const uint32_t hot = (p.dense && cl == 1) ? HB_HOT : 0;
+        const bool one = p.dense && cl == 1;  // one block per dense slot: k_heavy1
+        const uint32_t hot = one ? HB_HOT : 0;
         const size_t hsmem = hot * sizeof(uint32_t);
-        if (hsmem) PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
         hs.hot = hot;
-        int nc = max_clusters(kern, HB_THREADS, cl, hsmem);
+        int nc = 0;
+        if (one) {
+          PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+          int per_sm = 0;
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<PV, PE>, HB_THREADS, hsmem);
+          nc = sms * (per_sm > 0 ? per_sm : 1);
+        } else {
+          nc = max_clusters(kern, HB_THREADS, cl, hsmem);
+        }
         if (nc <= 0) nc = sms / static_cast<int>(cl);
         uint64_t nslots = static_cast<uint64_t>(nc);
         if (&pt == &parts[0] && p.max_slots && nslots > p.max_slots) nslots = p.max_slots;
@@ -1395,8 +1544,12 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         hs.item = hs.tcnt + 2 * nslots;
         if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-        if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list, pt.cnt,
-                                 hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) break;
+        if (one) {
+          PB_LAUNCH((k_heavy1<PV, PE>), static_cast<unsigned>(nslots), HB_THREADS, hsmem, s, a, pt.list, pt.cnt, hs);
+        } else if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list,
+                                        pt.cnt, hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) {
+          break;
+        }
       }
       if (st != PB_OK) break;
       ph.finish(s, hcnt[ACC_WHEAVY]);
