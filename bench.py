@@ -160,9 +160,10 @@ def measured_traffic(kernel: str, wedges_per_launch: float):
             sha = hashlib.sha256(f.read()).hexdigest()
     except Exception:
         return None
-    if t.get("kernel") != kernel or sha != t.get("source_sha256"):
+    k = t.get("kernels", {}).get(kernel)
+    if k is None or sha != t.get("source_sha256"):
         return None
-    return t["dram_bytes_per_wedge"] * wedges_per_launch
+    return k["dram_bytes_per_wedge"] * wedges_per_launch
 
 
 def measured_peaks():
