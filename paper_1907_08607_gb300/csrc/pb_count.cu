@@ -483,7 +483,6 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   __shared__ uint32_t s_incl[MB_THREADS], s_oy[MB_THREADS];  // per 32-chunk inclusive counts, first slots
   __shared__ unsigned long long s_sum[MB_THREADS];
-  __shared__ unsigned long long s_w64[33];
   __shared__ uint32_t s_item;
   const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   unsigned long long *err = &a0.acc[ACC_ERR];
@@ -492,9 +491,11 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
   if (s_hub) hub_zero(s_hub);
   for (uint32_t t = tid; t < MB_CAP; t += MB_THREADS) key[t] = EMPTY;
   for (uint32_t t = tid; t < MB_CAP / 2; t += MB_THREADS) cnt[t] = 0;
+  // The next owner is fetched by thread 0 during the previous owner's reset
+  // and published by the barrier that ends it.
+  if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
+  __syncthreads();
   for (;;) {
-    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
-    __syncthreads();
     const uint32_t it = s_item;
     if (it >= nlist) break;
     uint32_t x1;
@@ -509,7 +510,11 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
     }
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     if (wc > MED_MAX) {  // the tier split guarantees wc <= MED_MAX
-      if (tid == 0) atomicOr(err, 16ull);
+      __syncthreads();  // every thread has read s_item
+      if (tid == 0) {
+        atomicOr(err, 16ull);
+        s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
+      }
       __syncthreads();
       continue;
     }
@@ -562,11 +567,11 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
         if (PV && b) pv_add(s_hub, a, key[h], b);
       }
     }
-    own = block_sum(own, s_w64);
-    if (tid == 0) {
+    own = warp_sum(own);  // per warp: no block barrier
+    if (lane == 0 && own) {
       if (MULTI) add_global(a.acc, own);
       else gacc += own;
-      if (PV && own) atomicAdd(&a.pv[x1], own);
+      if (PV) atomicAdd(&a.pv[x1], own);
     }
     if (PV || PE) {
       done = 0;
@@ -613,11 +618,12 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
             s_sum[tid] = 0;
           }
         }
-        __syncthreads();
+        if (s0 + MB_THREADS < dp) __syncthreads();  // before the next group is staged
       }
     }
-    __syncthreads();
-    // reset the entries this owner used
+    // Reset the entries this owner used.  Entry h is read in the endpoint
+    // phase only by the thread of its flagged wedge, the one that resets it;
+    // the second pass ended with a barrier.
     for (uint32_t j = tid; j < nw; j += MB_THREADS) {
       const uint32_t p = pos[j];
       if (p & 0x8000u) {
@@ -626,9 +632,10 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
         atomicAnd(&cnt[h >> 1], (h & 1u) ? 0x0000ffffu : 0xffff0000u);
       }
     }
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QMED], 1ull));
     __syncthreads();
   }
-  if (!MULTI && tid == 0) add_global(a0.acc, gacc);
+  if (!MULTI && lane == 0) add_global(a0.acc, gacc);
   __syncthreads();
   if (s_hub) hub_flush(s_hub, a0);
 }
@@ -940,7 +947,6 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *
                                                        HeavySlots h) {
   extern __shared__ uint32_t hb_hot[];
   __shared__ uint32_t s_c[HB_THREADS], s_oy[HB_THREADS], s_y[HB_THREADS];
-  __shared__ unsigned long long s_w64[33];
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   __shared__ uint32_t s_item, s_next, s_nt;
   unsigned long long *s_hub = PV ? s_hubarr : nullptr;
@@ -1011,10 +1017,10 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *
       own += b;
       if (PV && b) pv_add(s_hub, a, x2, b);
     }
-    own = block_sum(own, s_w64);
-    if (tid == 0) {
+    own = warp_sum(own);  // per warp: no block barrier
+    if (lane == 0 && own) {
       gacc += own;
-      if (PV && own) atomicAdd(&a.pv[x1], own);
+      if (PV) atomicAdd(&a.pv[x1], own);
     }
     // ---- centres and edges: d - 1 per wedge
     if (PV || PE) {
@@ -1062,7 +1068,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *
     __syncthreads();
     if (tid == 0) s_nt = 0;
   }
-  if (tid == 0) add_global(a.acc, gacc);
+  if (lane == 0) add_global(a.acc, gacc);
   __syncthreads();
   if (s_hub) hub_flush(s_hub, a);
 }
