@@ -641,14 +641,16 @@ __global__ void __launch_bounds__(MB_THREADS, 3) k_medium(CArgs a0, const uint32
 }
 
 // ---------------------------------------------------------------------------
-// Heavy tier: one cluster per first endpoint; each cluster owns one slot of
-// device-memory scratch.  The blocks of the cluster walk the same neighbour
-// chunks and take equal shares of every chunk's wedges; inside a block
-// consecutive threads take consecutive wedges and every thread keeps HB_BATCH
-// of them in flight.  Phases are separated by cluster barriers
-// (release/acquire at cluster scope); scratch written by other blocks is read
-// through L2 (ld.global.cg).  A cluster of one block is plain batching: one
-// first endpoint per block and its own dense array.
+// Heavy tier, clustered or hashed (k_heavy): one cluster per first endpoint;
+// each cluster owns one slot of device-memory scratch.  Used for hubs (a
+// cluster of blocks each), for slots shared by a cluster when the scratch
+// budget holds fewer slots than there are SMs, for hash tables (HASH) and for
+// batches; a dense slot owned by one block uses k_heavy1 below.  The blocks of
+// the cluster walk the same neighbour chunks and take equal shares of every
+// chunk's wedges; inside a block consecutive threads take consecutive wedges
+// and every thread keeps HB_BATCH of them in flight.  Phases are separated by
+// cluster barriers (release/acquire at cluster scope); scratch written by
+// other blocks is read through L2 (ld.global.cg).
 // Dense slots are indexed by the second endpoint's offset within its side.
 constexpr int HB_BATCH = 4;
 // Shared-memory histogram of the first labels of a side: with the cache
@@ -664,7 +666,7 @@ struct HeavySlots {
   uint32_t *tcnt;     // [nslots][2] touched counters (alternating)
   uint32_t *item;     // [nslots] current work item of the slot
   uint64_t side, tcap, hcap;
-  uint32_t hot;       // dense, one block per slot: labels [0, hot) of the side counted in shared memory
+  uint32_t hot;       // k_heavy1: labels [0, hot) of the side counted in shared memory
 };
 
 // Appends second endpoints seen for the first time to the touched list
@@ -719,13 +721,9 @@ __device__ __forceinline__ void heavy_insert(const HeavySlots &h, uint32_t slot,
 }
 
 template <bool DENSE>
-__device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot, const uint32_t *A,
-                                              const uint32_t *hot, int lg, uint32_t x2, uint32_t base,
-                                              unsigned long long *err) {
-  if (DENSE) {
-    const uint32_t r = x2 - base;
-    return r < h.hot ? hot[r] : __ldcg(&A[r]);
-  }
+__device__ __forceinline__ uint32_t heavy_get(const HeavySlots &h, uint32_t slot, const uint32_t *A, int lg,
+                                              uint32_t x2, uint32_t base, unsigned long long *err) {
+  if (DENSE) return __ldcg(&A[x2 - base]);
   const uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
   const uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
   const uint32_t mask = (1u << lg) - 1;
@@ -751,15 +749,12 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
   __shared__ unsigned long long s_w64[33];
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
-  extern __shared__ uint32_t hb_hot[];  // h.hot counts (dense, one block per slot)
   uint32_t *A = DENSE ? h.A + static_cast<size_t>(slot) * h.side : nullptr;
   uint32_t *T = DENSE ? h.T + static_cast<size_t>(slot) * h.tcap : nullptr;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[tid] = 0;
   if (s_hub) hub_zero(s_hub);
-  if (DENSE)
-    for (uint32_t t = tid; t < h.hot; t += HB_THREADS) hb_hot[t] = 0;  // ordered by the first cluster barrier
   for (uint32_t k = 0;; k++) {
     if (crank == 0 && tid == 0) h.item[slot] = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QHEAVY], 1ull));
     cl.sync();
@@ -812,11 +807,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
           // issue every atomic of the batch before any result is used
           uint32_t old[HB_BATCH];
 #pragma unroll
-          for (int q = 0; q < HB_BATCH; q++) {
-            const uint32_t r = x2v[q] - base;
-            old[q] = wb + q * HB_THREADS + tid < hi ? (r < h.hot ? atomicAdd(&hb_hot[r], 1u) : atomicAdd(&A[r], 1u))
-                                                    : 1u;
-          }
+          for (int q = 0; q < HB_BATCH; q++)
+            old[q] = wb + q * HB_THREADS + tid < hi ? atomicAdd(&A[x2v[q] - base], 1u) : 1u;
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++) dense_touch(h, T, tc, x2v[q], old[q] == 0u, err);
         } else {
@@ -834,8 +826,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
       const uint32_t nt = __ldcg(tc);
       for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) {
         uint32_t x2 = __ldcg(&T[t]);
-        const uint32_t r = x2 - base;
-        unsigned long long d = r < h.hot ? hb_hot[r] : __ldcg(&A[r]), b = d * (d - 1) / 2;
+        unsigned long long d = __ldcg(&A[x2 - base]), b = d * (d - 1) / 2;
         own += b;
         if (PV && b) pv_add(s_hub, a, x2, b);
       }
@@ -889,7 +880,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
           }
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++)
-            dv[q] = wb + q * HB_THREADS + tid < hi ? heavy_get<DENSE>(h, slot, A, hb_hot, lg, x2v[q], base, err) : 0;
+            dv[q] = wb + q * HB_THREADS + tid < hi ? heavy_get<DENSE>(h, slot, A, lg, x2v[q], base, err) : 0;
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++) {
             unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
@@ -913,11 +904,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
     // ---- restore the slot to all-zero / all-empty
     if (DENSE) {
       const uint32_t nt = __ldcg(tc);
-      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) {
-        const uint32_t r = __ldcg(&T[t]) - base;
-        if (r < h.hot) hb_hot[r] = 0;
-        else A[r] = 0;
-      }
+      for (uint32_t t = crank * HB_THREADS + tid; t < nt; t += csize * HB_THREADS) A[__ldcg(&T[t]) - base] = 0;
     } else {
       uint32_t *key = h.hkey + static_cast<size_t>(slot) * h.hcap;
       uint32_t *val = h.hval + static_cast<size_t>(slot) * h.hcap;
@@ -942,28 +929,38 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
 // slot's device-memory histogram; a touched list (device memory, counter in
 // shared memory) records each distinct second endpoint once.  The second
 // pass sums d - 1 over a segment in registers and adds it to the centre once.
-template <bool PV, bool PE>
-__global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *__restrict__ list, uint32_t nlist,
-                                                       HeavySlots h) {
+template <bool PV, bool PE, bool MULTI>
+__global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
+                                                       HeavySlots h, const uint64_t *__restrict__ items,
+                                                       const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t hb_hot[];
   __shared__ uint32_t s_c[HB_THREADS], s_oy[HB_THREADS], s_y[HB_THREADS];
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   __shared__ uint32_t s_item, s_next, s_nt;
-  unsigned long long *s_hub = PV ? s_hubarr : nullptr;
+  unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   const uint32_t slot = blockIdx.x, tid = threadIdx.x, lane = lane_id();
   uint32_t *A = h.A + static_cast<size_t>(slot) * h.side;
   uint32_t *T = h.T + static_cast<size_t>(slot) * h.tcap;
-  unsigned long long *err = &a.acc[ACC_ERR];
+  unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (s_hub) hub_zero(s_hub);
   for (uint32_t t = tid; t < h.hot; t += HB_THREADS) hb_hot[t] = 0;
   if (tid == 0) s_nt = 0;
   for (;;) {
-    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QHEAVY], 1ull));
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QHEAVY], 1ull));
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= nlist) break;
-    const uint32_t x1 = list[it];
+    uint32_t x1;
+    CArgs a;  // this item's graph
+    if (MULTI) {
+      const uint64_t item = items[it];
+      a = tab[item >> 32];
+      x1 = static_cast<uint32_t>(item);
+    } else {
+      a = a0;
+      x1 = list[it];
+    }
     const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
     const uint32_t xbase = a.off[x1], dp = owner_span(a, x1);
     // ---- aggregate
@@ -1019,7 +1016,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *
     }
     own = warp_sum(own);  // per warp: no block barrier
     if (lane == 0 && own) {
-      gacc += own;
+      if (MULTI) add_global(a.acc, own);
+      else gacc += own;
       if (PV) atomicAdd(&a.pv[x1], own);
     }
     // ---- centres and edges: d - 1 per wedge
@@ -1068,9 +1066,9 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a, const uint32_t *
     __syncthreads();
     if (tid == 0) s_nt = 0;
   }
-  if (lane == 0) add_global(a.acc, gacc);
+  if (!MULTI && lane == 0) add_global(a0.acc, gacc);
   __syncthreads();
-  if (s_hub) hub_flush(s_hub, a);
+  if (s_hub) hub_flush(s_hub, a0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1520,9 +1518,10 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         hs.hot = hot;
         int nc = 0;
         if (one) {
-          PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+          PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)hsmem));
           int per_sm = 0;
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<PV, PE>, HB_THREADS, hsmem);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<PV, PE, false>, HB_THREADS, hsmem);
           nc = sms * (per_sm > 0 ? per_sm : 1);
         } else {
           nc = max_clusters(kern, HB_THREADS, cl, hsmem);
@@ -1551,7 +1550,8 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         if (one) {
-          PB_LAUNCH((k_heavy1<PV, PE>), static_cast<unsigned>(nslots), HB_THREADS, hsmem, s, a, pt.list, pt.cnt, hs);
+          PB_LAUNCH((k_heavy1<PV, PE, false>), static_cast<unsigned>(nslots), HB_THREADS, hsmem, s, a, pt.list, pt.cnt,
+                    hs, (const uint64_t *)nullptr, (const CArgs *)nullptr);
         } else if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list,
                                         pt.cnt, hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) {
           break;
@@ -1941,6 +1941,8 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
                                (int)(LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t))));
   PB_CUDA(cudaFuncSetAttribute(k_medium<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)MB_SMEM));
+  PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(b->hs.hot * sizeof(uint32_t))));
   PB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   pb_status st = PB_OK;
   do {
@@ -1976,9 +1978,11 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
     if (b->nh) {
       e1 = cudaMemsetAsync(b->scratch, 0, b->nslots * b->slot_bytes + b->nslots * 7 * sizeof(uint32_t) + 64, s);
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (slots)", __FILE__, __LINE__); break; }
-      if ((st = launch_cluster(k_heavy<PV, false, true, true>, static_cast<unsigned>(b->nslots), HB_THREADS, 1, 0, s, a0,
-                               (const uint32_t *)nullptr, b->nh, b->hs, (const uint64_t *)b->heavy,
-                               (const CArgs *)b->tab)) != PB_OK) break;
+      k_heavy1<PV, false, true><<<static_cast<unsigned>(b->nslots), HB_THREADS, b->hs.hot * sizeof(uint32_t), s>>>(
+          a0, nullptr, b->nh, b->hs, b->heavy, b->tab);
+      count_launch();
+      e1 = cudaGetLastError();
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch heavy launch", __FILE__, __LINE__); break; }
     }
   } while (0);
   cudaGraph_t graph = nullptr;
@@ -2074,8 +2078,12 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
     b->hs.side = max_side;
     b->hs.tcap = max_bound < max_side ? max_bound : max_side;
     b->slot_bytes = (b->hs.side + b->hs.tcap) * sizeof(uint32_t);
+    b->hs.hot = HB_HOT;
+    const size_t hsmem = HB_HOT * sizeof(uint32_t);
+    PB_CUDA(cudaFuncSetAttribute(k_heavy1<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+    PB_CUDA(cudaFuncSetAttribute(k_heavy1<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy<true, false, true, true>, HB_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<true, false, true>, HB_THREADS, hsmem);
     uint64_t ns = static_cast<uint64_t>(sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
     uint64_t fit = budget / (b->slot_bytes + 32);
     if (fit == 0) return fail(PB_ERR_SCRATCH, "batch scratch budget below one slot");
