@@ -36,17 +36,28 @@ __global__ void k_canon(const uint64_t *__restrict__ keys, const uint32_t *__res
                         int bitsV, uint32_t nU, uint32_t *__restrict__ in2c, uint32_t *__restrict__ eu,
                         uint32_t *__restrict__ ev, uint32_t *__restrict__ deg) {
   const uint64_t maskV = (uint64_t(1) << bitsV) - 1;
-  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t r = cid[i] + head[i] - 1;
-    in2c[idx[i]] = r;
-    if (head[i]) {
-      uint32_t a = static_cast<uint32_t>(keys[i] >> bitsV), b = static_cast<uint32_t>(keys[i] & maskV);
-      eu[r] = a;
-      ev[r] = b;
-      atomicAdd(&deg[a], 1u);
-      atomicAdd(&deg[nU + b], 1u);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t iters = (m + stride - 1) / stride;
+  for (size_t itn = 0; itn < iters; itn++) {  // uniform trip count: the whole warp reaches the matches
+    const size_t i = start + itn * stride;
+    uint32_t du = 0xffffffffu, dv = 0xffffffffu;  // degree targets of this canonical edge
+    if (i < m) {
+      uint32_t r = cid[i] + head[i] - 1;
+      in2c[idx[i]] = r;
+      if (head[i]) {
+        uint32_t a = static_cast<uint32_t>(keys[i] >> bitsV), b = static_cast<uint32_t>(keys[i] & maskV);
+        eu[r] = a;
+        ev[r] = b;
+        du = a;
+        dv = nU + b;
+      }
     }
+    // keys are sorted by u, so a warp's edges mostly share u: one atomic per distinct vertex
+    uint32_t peers = __match_any_sync(FULL, du);
+    if (du != 0xffffffffu && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&deg[du], __popc(peers));
+    peers = __match_any_sync(FULL, dv);
+    if (dv != 0xffffffffu && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&deg[dv], __popc(peers));
   }
 }
 
@@ -385,51 +396,43 @@ __global__ void k_arcs_out(const uint32_t *__restrict__ vals, uint64_t na, const
 // of y's neighbours ranked above x, since lists are strictly decreasing in
 // rank); degp[x] = deg_x(x), the length of the prefix of x's list ranked above
 // x.  Neighbour ranks come from the sort keys, the owner's from lrank.
+// The same pass adds, for the lower-endpoint owner x, the wedges through
+// every neighbour of its prefix: wedges(x) = sum of cpos over the first
+// degp[x] slots of x (warp-aggregated atomics into wc).
 __global__ void k_cpos_degp(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                             uint64_t na, int bitsN, const uint32_t *__restrict__ off,
                             const uint32_t *__restrict__ adj, const uint32_t *__restrict__ slotA,
                             const uint32_t *__restrict__ slotB, const uint32_t *__restrict__ lrank,
-                            uint32_t *__restrict__ cpos, uint32_t *__restrict__ degp) {
+                            uint32_t *__restrict__ cpos, uint32_t *__restrict__ degp,
+                            unsigned long long *__restrict__ wc) {
   const uint64_t mask = (uint64_t(1) << bitsN) - 1;
-  for (size_t s = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < na;
-       s += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t a = vals[s];
-    uint32_t other = (a & 1u) ? slotA[a >> 1] : slotB[a >> 1];
-    cpos[s] = other - off[adj[s]];
-    uint32_t x = static_cast<uint32_t>(keys[s] >> bitsN);
-    uint32_t rx = lrank[x];
-    uint32_t ry = static_cast<uint32_t>(mask - (keys[s] & mask));
-    if (ry > rx) {
-      bool last = s + 1 == off[x + 1];
-      if (!last) last = static_cast<uint32_t>(mask - (keys[s + 1] & mask)) < rx;
-      if (last) degp[x] = static_cast<uint32_t>(s + 1 - off[x]);
-    }
-  }
-}
-
-// wedges(x) = sum over the first degp[x] slots of x of cpos; warp-aggregated.
-__global__ void k_wedges_per_x(const uint64_t *__restrict__ keys, uint64_t na, int bitsN,
-                               const uint32_t *__restrict__ off, const uint32_t *__restrict__ degp,
-                               const uint32_t *__restrict__ cpos, unsigned long long *__restrict__ wc) {
-  size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-  size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  size_t iters = (na + stride - 1) / stride;
-  for (size_t it = 0; it < iters; it++) {
-    size_t s = start + it * stride;
-    bool valid = s < na;
-    uint32_t x = valid ? static_cast<uint32_t>(keys[s] >> bitsN) : 0xffffffffu;
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t iters = (na + stride - 1) / stride;
+  for (size_t itn = 0; itn < iters; itn++) {  // uniform trip count: the whole warp reaches the match
+    const size_t s = start + itn * stride;
+    const bool valid = s < na;
+    uint32_t x = 0xffffffffu;
     unsigned long long c = 0;
-    if (valid && s - off[x] < degp[x]) c = cpos[s];
-    uint32_t peers = __match_any_sync(FULL, x);
-    // sum c over the peer group, result in its lowest lane
-    uint32_t leader = __ffs(peers) - 1;
-    unsigned long long tot = 0;
-    for (uint32_t p = peers; p; p &= p - 1) {
-      uint32_t l = __ffs(p) - 1;
-      unsigned long long cl = __shfl_sync(peers, c, l);
-      tot += cl;
+    if (valid) {
+      uint32_t a = vals[s];
+      uint32_t other = (a & 1u) ? slotA[a >> 1] : slotB[a >> 1];
+      const uint32_t cp = other - off[adj[s]];
+      cpos[s] = cp;
+      x = static_cast<uint32_t>(keys[s] >> bitsN);
+      uint32_t rx = lrank[x];
+      uint32_t ry = static_cast<uint32_t>(mask - (keys[s] & mask));
+      if (ry > rx) {
+        c = cp;
+        bool last = s + 1 == off[x + 1];
+        if (!last) last = static_cast<uint32_t>(mask - (keys[s + 1] & mask)) < rx;
+        if (last) degp[x] = static_cast<uint32_t>(s + 1 - off[x]);
+      }
     }
-    if (valid && lane_id() == leader && tot) atomicAdd(&wc[x], tot);
+    const uint32_t peers = __match_any_sync(FULL, x);
+    unsigned long long tot = 0;
+    for (uint32_t q = peers; q; q &= q - 1) tot += __shfl_sync(peers, c, __ffs(q) - 1);
+    if (valid && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1) && tot) atomicAdd(&wc[x], tot);
   }
 }
 
@@ -595,11 +598,9 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(vals, na, g->eu, g->ev, g->nU, g->label, g->adj, g->slotA,
                                                          g->slotB);
       count_launch();
+      // ---- 4. (same pass) wedges per first endpoint, then the work split prefix
       k_cpos_degp<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->off, g->adj, g->slotA,
-                                                           g->slotB, lrank, g->cpos, g->degp);
-      count_launch();
-      // ---- 4. wedges per first endpoint and the work split prefix
-      k_wedges_per_x<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, na, bitsN, g->off, g->degp, g->cpos, wc);
+                                                           g->slotB, lrank, g->cpos, g->degp, wc);
       count_launch();
     }
     if ((st = scan_u64(reinterpret_cast<uint64_t *>(wc), g->wpre, n, s)) != PB_OK) break;
