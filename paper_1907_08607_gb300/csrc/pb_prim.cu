@@ -159,11 +159,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
   const size_t wbase = tbase + static_cast<size_t>(w) * 32 * RS_IPT;
   uint64_t k[RS_IPT];
   uint32_t lr[RS_IPT];
+  // all of the thread's keys are loaded before the ranking starts (the warp
+  // barriers of the ranking would otherwise hold each load back)
+  uint32_t vv[VALS ? RS_IPT : 1];
+#pragma unroll
+  for (int r = 0; r < RS_IPT; r++) {
+    size_t i = wbase + static_cast<size_t>(r) * 32 + lane;
+    k[r] = i < n ? kin[i] : 0;
+    if (VALS) vv[r] = i < n ? vin[i] : 0;
+  }
 #pragma unroll
   for (int r = 0; r < RS_IPT; r++) {
     size_t i = wbase + static_cast<size_t>(r) * 32 + lane;
     bool valid = i < n;
-    k[r] = valid ? kin[i] : 0;
     uint32_t d = valid ? static_cast<uint32_t>((k[r] >> shift) & (RS_BINS - 1)) : 0xffffffffu;
     uint32_t peers = __match_any_sync(FULL, d);
     uint32_t cur = valid ? wcnt[w][d] : 0;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
       uint32_t d = static_cast<uint32_t>((k[r] >> shift) & (RS_BINS - 1));
       uint32_t lp = tstart[d] + wcnt[w][d] + lr[r];
       skey[lp] = k[r];
-      if (VALS) sval[lp] = vin[i];
+      if (VALS) sval[lp] = vv[r];
     }
   }
   __syncthreads();
