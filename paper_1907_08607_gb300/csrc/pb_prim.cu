@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restri
 // digit-sorted order and written out in runs, so consecutive threads write
 // consecutive output positions.
 template <bool VALS>
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, size_t n, int shift, const uint32_t *__restrict__ offs,
     uint32_t ntiles) {
