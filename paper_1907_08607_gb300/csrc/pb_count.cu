@@ -1338,14 +1338,22 @@ __global__ void k_out_vertex(const unsigned long long *__restrict__ pv, const ui
   }
 }
 
-__global__ void k_out_edge(const unsigned long long *__restrict__ es, const uint32_t *__restrict__ slotA,
-                           const uint32_t *__restrict__ slotB, const uint32_t *__restrict__ in2c, uint64_t m_in,
+// Per-edge count of canonical edge e = the sums on its two adjacency slots.
+// Canonical edges are ordered by U endpoint, so slotA reads stay within one
+// list for runs of edges.
+__global__ void k_edge_sums(const unsigned long long *__restrict__ es, const uint32_t *__restrict__ slotA,
+                            const uint32_t *__restrict__ slotB, uint64_t m, uint64_t *__restrict__ E) {
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x)
+    E[e] = es[slotA[e]] + es[slotB[e]];
+}
+
+// Input pair k reports the count of its canonical edge.
+__global__ void k_out_edge(const uint64_t *__restrict__ E, const uint32_t *__restrict__ in2c, uint64_t m_in,
                            uint64_t *__restrict__ outE) {
   for (size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < m_in;
-       k += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t e = in2c[k];
-    outE[k] = es[slotA[e]] + es[slotB[e]];
-  }
+       k += static_cast<size_t>(gridDim.x) * blockDim.x)
+    outE[k] = E[in2c[k]];
 }
 
 // ---------------------------------------------------------------------------
@@ -1820,10 +1828,16 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
                                                          g->nU, g->nV, dU, dV);
     count_launch();
   }
+  uint64_t *Ecan = nullptr;
   if (want_pe && g->m_in) {
-    k_out_edge<<<grid_for(g->m_in, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->es),
-                                                             g->slotA, g->slotB, g->in2c, g->m_in, dE);
-    count_launch();
+    st = dalloc_t(&Ecan, g->m + 1, s);
+    if (st == PB_OK) {
+      k_edge_sums<<<grid_for(g->m, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->es), g->slotA,
+                                                            g->slotB, g->m, Ecan);
+      count_launch();
+      k_out_edge<<<grid_for(g->m_in, 256, 8192), 256, 0, s>>>(Ecan, g->in2c, g->m_in, dE);
+      count_launch();
+    }
   }
   if (cudaGetLastError() != cudaSuccess) st = fail(PB_ERR_CUDA, "output kernels failed to launch");
   if (st == PB_OK && !o.on_device) {
@@ -1833,6 +1847,7 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     if (e == cudaSuccess && o.E && g->m_in) e = cudaMemcpyAsync(o.E, dE, g->m_in * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) st = cuda_fail(e, "output download", __FILE__, __LINE__);
   }
+  dfree(Ecan, s);
   dfree(tmp, s);
   if (st == PB_OK) ph_out.finish(s);
   cudaError_t e = cudaStreamSynchronize(s);
