@@ -351,13 +351,14 @@ __global__ void k_is_u(const uint32_t *__restrict__ order, uint64_t n, uint32_t 
 
 __global__ void k_labels(const uint32_t *__restrict__ order, const uint32_t *__restrict__ cu, uint64_t n,
                          uint32_t nU, const uint32_t *__restrict__ deg, uint32_t *__restrict__ label,
-                         uint32_t *__restrict__ lrank, uint32_t *__restrict__ degl) {
+                         uint32_t *__restrict__ lrank, uint32_t *__restrict__ rlab, uint32_t *__restrict__ degl) {
   for (size_t r = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
        r += static_cast<size_t>(gridDim.x) * blockDim.x) {
     uint32_t x = order[r];
     uint32_t l = x < nU ? cu[r] : nU + static_cast<uint32_t>(r - cu[r]);
     label[x] = l;
     lrank[l] = static_cast<uint32_t>(r);
+    rlab[r] = l;
     degl[l] = deg[x];
   }
 }
@@ -376,19 +377,19 @@ __global__ void k_arc_keys(const uint32_t *__restrict__ eu, const uint32_t *__re
   }
 }
 
-__global__ void k_arcs_out(const uint32_t *__restrict__ vals, uint64_t na, const uint32_t *__restrict__ eu,
-                           const uint32_t *__restrict__ ev, uint32_t nU, const uint32_t *__restrict__ label,
-                           uint32_t *__restrict__ adj, uint32_t *__restrict__ slotA, uint32_t *__restrict__ slotB) {
+// Slot s holds the arc of sort key keys[s]: its neighbour's label comes from
+// the rank in the key (rlab: label of each rank, a table that stays in L2),
+// and the arc's edge learns its slot.
+__global__ void k_arcs_out(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint64_t na,
+                           int bitsN, const uint32_t *__restrict__ rlab, uint32_t *__restrict__ adj,
+                           uint32_t *__restrict__ slotA, uint32_t *__restrict__ slotB) {
+  const uint64_t mask = (uint64_t(1) << bitsN) - 1;
   for (size_t s = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < na;
        s += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t a = vals[s], e = a >> 1;
-    if (a & 1u) {  // arc from v to u
-      adj[s] = label[eu[e]];
-      slotB[e] = static_cast<uint32_t>(s);
-    } else {
-      adj[s] = label[nU + ev[e]];
-      slotA[e] = static_cast<uint32_t>(s);
-    }
+    const uint32_t a = vals[s], e = a >> 1;
+    adj[s] = rlab[mask - (keys[s] & mask)];
+    if (a & 1u) slotB[e] = static_cast<uint32_t>(s);  // arc from v to u
+    else slotA[e] = static_cast<uint32_t>(s);
   }
 }
 
@@ -509,7 +510,7 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
   pb_status st = alloc_ranked(g, s);
   if (st != PB_OK) { free_ranked(g, s); return st; }
   uint64_t *keys = nullptr;
-  uint32_t *vals = nullptr, *tmp = nullptr, *drank = nullptr, *lrank = nullptr, *cu = nullptr;
+  uint32_t *vals = nullptr, *tmp = nullptr, *drank = nullptr, *lrank = nullptr, *cu = nullptr, *rlab = nullptr;
   unsigned long long *acc = nullptr, *wc = nullptr;
   unsigned long long hacc[2] = {0, 0};
   do {
@@ -572,13 +573,14 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
     if ((st = dalloc_t(&tmp, n + 1, s)) != PB_OK) break;
     if ((st = dalloc_t(&cu, n + 1, s)) != PB_OK) break;
     if ((st = dalloc_t(&lrank, n + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&rlab, n + 1, s)) != PB_OK) break;
     if (n) {
       k_is_u<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->order, n, g->nU, tmp);
       count_launch();
     }
     if ((st = scan_u32(tmp, cu, n, s)) != PB_OK) break;
     if (n) {
-      k_labels<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->order, cu, n, g->nU, g->deg, g->label, lrank, tmp);
+      k_labels<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->order, cu, n, g->nU, g->deg, g->label, lrank, rlab, tmp);
       count_launch();
     }
     if ((st = scan_u32(tmp, g->off, n, s)) != PB_OK) break;
@@ -595,8 +597,7 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
                                                          vals);
       count_launch();
       if ((st = radix_sort(keys, vals, na, 2 * bitsN, s)) != PB_OK) break;
-      k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(vals, na, g->eu, g->ev, g->nU, g->label, g->adj, g->slotA,
-                                                         g->slotB);
+      k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, rlab, g->adj, g->slotA, g->slotB);
       count_launch();
       // ---- 4. (same pass) wedges per first endpoint, then the work split prefix
       k_cpos_degp<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->off, g->adj, g->slotA,
@@ -632,7 +633,7 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
     g->rank_kind = rank_of ? 5 : kind;
   } while (0);
   dfree(keys, s); dfree(vals, s); dfree(tmp, s); dfree(drank, s); dfree(acc, s); dfree(wc, s);
-  dfree(lrank, s); dfree(cu, s);
+  dfree(lrank, s); dfree(cu, s); dfree(rlab, s);
   if (st != PB_OK) free_ranked(g, s);
   return st;
 }
