@@ -314,7 +314,8 @@ def run_gb300(args):
             G.count_all(args.agg, on_device=False, out=hout)
             G.free()
 
-        step_host()
+        for _ in range(max(3, args.warmup)):
+            step_host()
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
