@@ -310,7 +310,7 @@ __device__ __forceinline__ void warp_run_add_rx(unsigned long long *acc, uint32_
 // ---------------------------------------------------------------------------
 // Light tier: one warp per owner; per-warp table with 16-bit counts; LW_BATCH
 // steps of 32 wedges in flight per warp.
-constexpr int LW_BATCH = 4;
+constexpr int LW_BATCH = 2;
 
 template <bool PV, bool PE, bool MULTI>
 __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_t *__restrict__ list,
