@@ -180,6 +180,14 @@ __device__ __forceinline__ void owner_nbr(const CArgs &a, uint32_t xbase, uint32
   oy = o0 + st;
 }
 
+// First label a dense histogram of owner x1 covers: its second endpoints are
+// the labels of its side below x1 (owner = higher-ranked endpoint) or above
+// it (owner = lower-ranked endpoint), so a histogram of the owner's range of
+// labels suffices.
+__device__ __forceinline__ uint32_t dense_base(const CArgs &a, uint32_t x1) {
+  return a.rev ? (x1 < a.nU ? 0u : a.nU) : x1 + 1;
+}
+
 // Number of neighbours of owner x that can carry its wedges.
 __device__ __forceinline__ uint32_t owner_span(const CArgs &a, uint32_t x) {
   return a.rev ? a.off[x + 1] - a.off[x] : a.degp[x];
@@ -772,7 +780,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
       a = a0;
       x1 = list[it];
     }
-    const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
+    const uint32_t base = dense_base(a, x1);  // label of histogram entry 0
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     const int lg = DENSE ? 0 : table_lg(wc, a.n, a.nU, x1, a.rev);
     const uint32_t xbase = a.off[x1], dp = owner_span(a, x1);
@@ -961,7 +969,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t 
       a = a0;
       x1 = list[it];
     }
-    const uint32_t base = x1 < a.nU ? 0u : a.nU;  // first label of x1's side
+    const uint32_t base = dense_base(a, x1);  // label of histogram entry 0
     const uint32_t xbase = a.off[x1], dp = owner_span(a, x1);
     // ---- aggregate
     for (uint32_t s0 = 0; s0 < dp; s0 += HB_THREADS) {
@@ -1306,21 +1314,29 @@ __global__ void k_keys_low(const uint64_t *__restrict__ keys, uint32_t nk, int b
     out[i] = static_cast<uint32_t>(keys[i] & mask);
 }
 
+// out[0] = the largest bound on distinct second endpoints over the listed
+// owners; out[1] = the largest range of labels their second endpoints can
+// take (the length of a dense histogram for them).
 __global__ void k_max_wedges_list(const uint32_t *__restrict__ list, uint32_t nl, const uint64_t *__restrict__ wpre,
                                   uint64_t n, uint32_t nU, int rev, unsigned long long *out) {
-  unsigned long long mx = 0;
+  unsigned long long mx = 0, mr = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
     uint32_t x = list[i];
     unsigned long long dm = distinct_bound(wpre[x + 1] - wpre[x], n, nU, x, rev);
+    unsigned long long rm = distinct_bound(~0ull, n, nU, x, rev);
     mx = dm > mx ? dm : mx;
+    mr = rm > mr ? rm : mr;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    unsigned long long y = __shfl_xor_sync(FULL, mx, o);
+    unsigned long long y = __shfl_xor_sync(FULL, mx, o), z = __shfl_xor_sync(FULL, mr, o);
     mx = y > mx ? y : mx;
+    mr = z > mr ? z : mr;
   }
-  if (lane_id() == 0 && mx) atomicMax(out, mx);
+  if (lane_id() == 0 && mx) atomicMax(&out[0], mx);
+  if (lane_id() == 0 && mr) atomicMax(&out[1], mr);
 }
+
 
 // ---------------------------------------------------------------------------
 // Outputs back in id space / input order.
@@ -1471,15 +1487,17 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
       if ((st = dalloc_t(&heavy, nh, s)) != PB_OK) break;
       k_keys_low<<<grid_for(nh, 256, 4096), 256, 0, s>>>(hkeys, nh, g->bitsN, heavy);
       count_launch();
-      if ((st = dalloc_t(&dmx, 1, s)) != PB_OK) break;
-      if (cudaMemsetAsync(dmx, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      if ((st = dalloc_t(&dmx, 2, s)) != PB_OK) break;
+      if (cudaMemsetAsync(dmx, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
       k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, a.wpre, n, g->nU, a.rev, dmx);
       count_launch();
-      unsigned long long hdm = 0;
-      if (cudaMemcpyAsync(&hdm, dmx, sizeof(hdm), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      unsigned long long hdm2[2] = {0, 0};
+      if (cudaMemcpyAsync(hdm2, dmx, sizeof(hdm2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "heavy readback"); break; }
+      const unsigned long long hdm = hdm2[0];
       HeavySlots hs = {};
       hs.side = g->nU > g->nV ? g->nU : g->nV;
+      if (hdm2[1] && hdm2[1] < hs.side) hs.side = hdm2[1];  // dense histograms span the owners' label ranges
       size_t slot_bytes;
       if (p.dense) {
         hs.tcap = hdm < hs.side ? hdm : hs.side;
@@ -2036,7 +2054,7 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
   uint64_t *th = nullptr;
   unsigned long long *tacc = nullptr;
   pb_status st = PB_OK;
-  uint64_t max_bound = 1;
+  uint64_t max_bound = 1, max_room = 1;
   do {
     if ((st = dalloc_t(&tacc, ACC_WORDS, s)) != PB_OK) break;
     for (uint32_t i = 0; i < ng && st == PB_OK; i++) {
@@ -2072,13 +2090,14 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
         k_tag_items<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, i, b->heavy + b->nh);
         count_launch();
         // distinct bound of this graph's heavy owners
-        if (cudaMemsetAsync(tacc, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+        if (cudaMemsetAsync(tacc, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         k_max_wedges_list<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, a.wpre, n, g->nU, a.rev, tacc);
         count_launch();
-        unsigned long long bd = 0;
-        if (cudaMemcpyAsync(&bd, tacc, sizeof(bd), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        unsigned long long bd[2] = {0, 0};
+        if (cudaMemcpyAsync(bd, tacc, sizeof(bd), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
-        if (bd > max_bound) max_bound = bd;
+        if (bd[0] > max_bound) max_bound = bd[0];
+        if (bd[1] > max_room) max_room = bd[1];
       }
       b->nl += cl; b->nm += cm; b->nh += ch;
       dfree(tl, s); dfree(tm, s); dfree(th, s);
@@ -2090,7 +2109,7 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
   PB_TRY(dalloc_t(&b->tab, ng, s));
   PB_CUDA(cudaMemcpyAsync(b->tab, host_tab.data(), sizeof(CArgs) * ng, cudaMemcpyHostToDevice, s));
   if (b->nh) {
-    b->hs.side = max_side;
+    b->hs.side = max_room < max_side ? max_room : max_side;  // dense histograms span the owners' label ranges
     b->hs.tcap = max_bound < max_side ? max_bound : max_side;
     b->slot_bytes = (b->hs.side + b->hs.tcap) * sizeof(uint32_t);
     b->hs.hot = HB_HOT;
