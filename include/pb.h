@@ -70,11 +70,11 @@ typedef enum {
  *  HIST:  as HASH for light first endpoints; heavy (low-rank) first endpoints
  *         count their wedges in a dense histogram over all second endpoints,
  *         shared by a thread-block cluster.
- *  BATCH: dense arrays over all second endpoints, one per concurrently
- *         processed first endpoint, as many as the scratch budget holds
- *         (simple batching); first endpoints are taken in decreasing order of
- *         wedge count (wedge-aware).  First endpoints with few wedges use
- *         shared-memory tables.
+ *  BATCH: dense arrays over the range of second endpoints, one per
+ *         concurrently processed first endpoint, as many as the scratch
+ *         budget holds (simple batching), one block each; first endpoints are
+ *         taken in decreasing order of wedge count (wedge-aware).  First
+ *         endpoints with at most 4096 wedges use shared-memory tables.
  *  AUTO:  chosen per graph from degree and wedge statistics. */
 typedef enum {
   PB_AGG_SORT = 0,

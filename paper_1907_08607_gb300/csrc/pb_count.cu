@@ -1800,7 +1800,9 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
     p.max_slots = env_u64("PB_HEAVY_SLOTS", 0);
     p.hub_min = env_u64("PB_HUB_MIN", plan.hub_min);
     if (agg == PB_AGG_BATCH) {
-      p.med_max = LIGHT_MAX;  // everything above the light tier uses dense arrays
+      // One dense array per concurrently processed heavy first endpoint, no
+      // clusters; first endpoints with at most MED_MAX wedges keep the
+      // shared-memory tiers (a dense array each would exhaust the budget).
       p.cluster = 1;
       p.max_slots = 0;
       p.hub_min = UINT64_MAX;
