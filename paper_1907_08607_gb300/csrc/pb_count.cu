@@ -62,6 +62,7 @@ constexpr uint32_t LIGHT_MAX = 512;   // wedges of a light first endpoint
 constexpr int LW_THREADS = 512;
 constexpr int LW_WARPS = LW_THREADS / 32;
 constexpr int LW_CAP = 1024;          // per-warp table entries (>= 2 * LIGHT_MAX)
+constexpr int LW_LG = 10;
 constexpr uint32_t MED_MAX = 4096;
 constexpr int MB_THREADS = 512;
 constexpr int MB_WARPS = MB_THREADS / 32;
@@ -235,6 +236,29 @@ __device__ __forceinline__ uint32_t sh_add16f(uint32_t *key, uint32_t *cnt16, in
   return h | (((old >> sh) & 0xffffu) == 0 ? 0x8000u : 0u);
 }
 
+// As sh_add16, also setting bit h of the occupancy bitmap occ when x takes a
+// new entry h.
+__device__ __forceinline__ void sh_add16m(uint32_t *key, uint32_t *cnt16, uint32_t *occ, int lg, uint32_t x,
+                                          unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t h = hash_home(x, lg);
+  for (uint32_t probe = 0;; probe++) {
+    if (probe > mask) { atomicOr(err, 1ull); return; }
+    uint32_t k = reinterpret_cast<volatile uint32_t *>(key)[h];
+    if (k == x) break;
+    if (k == EMPTY) {
+      uint32_t prev = atomicCAS(&key[h], EMPTY, x);
+      if (prev == EMPTY) {
+        atomicOr(&occ[h >> 5], 1u << (h & 31u));
+        break;
+      }
+      if (prev == x) break;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicAdd(&cnt16[h >> 1], 1u << ((h & 1u) << 4));
+}
+
 __device__ __forceinline__ uint32_t cnt16_at(const uint32_t *cnt16, uint32_t h) {
   return (cnt16[h >> 1] >> ((h & 1u) << 4)) & 0xffffu;
 }
@@ -326,14 +350,22 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
                                                       const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP / 2 count words
   __shared__ unsigned long long s_sum[LW_WARPS][32];
+  __shared__ uint32_t s_occ[LW_WARPS][LW_CAP / 32];  // per warp: occupied table entries
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-  uint32_t *key = dsm + w * (LW_CAP + LW_CAP / 2), *cnt = key + LW_CAP;
+  uint32_t *key = dsm + w * (LW_CAP + LW_CAP / 2), *cnt = key + LW_CAP, *occ = s_occ[w];
+  static_assert(LW_CAP == 32 * 32, "one bitmap word of 32 entries per lane");
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (PV || PE) s_sum[w][lane] = 0;
   if (s_hub) hub_zero(s_hub);
+  // The table always has LW_CAP entries and is cleared once; each owner marks
+  // the entries it takes in occ, and its endpoint phase and reset visit only
+  // those (lane l owns entries [32 l, 32 l + 32) and count words [16 l, 16 l + 16)).
+  for (uint32_t t = lane; t < LW_CAP; t += 32) key[t] = EMPTY;
+  for (uint32_t t = lane; t < LW_CAP / 2; t += 32) cnt[t] = 0;
+  occ[lane] = 0;
   __syncthreads();
   for (uint32_t it = blockIdx.x * LW_WARPS + w; it < nlist; it += gridDim.x * LW_WARPS) {
     uint32_t x1;
@@ -346,12 +378,7 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
       a = a0;
       x1 = list[it];
     }
-    const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
-    const int lg = table_lg(wc, a.n, a.nU, x1, a.rev);
-    const uint32_t cap = 1u << lg;
-    for (uint32_t t = lane; t < cap; t += 32) key[t] = EMPTY;
-    for (uint32_t t = lane; t < cap / 2; t += 32) cnt[t] = 0;
-    __syncwarp();
+    const int lg = LW_LG;
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     // An owner with at most 32 neighbours has one chunk: its neighbour data
     // stay in registers for the second pass.
@@ -374,18 +401,16 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
         }
 #pragma unroll
         for (int q = 0; q < LW_BATCH; q++)
-          if (wb + q * 32 + lane < tot) sh_add16(key, cnt, lg, x2v[q], err);
+          if (wb + q * 32 + lane < tot) sh_add16m(key, cnt, occ, lg, x2v[q], err);
       }
     }
     __syncwarp();
     unsigned long long own = 0;
-    for (uint32_t t = lane; t < cap; t += 32) {
-      uint32_t k = key[t];
-      if (k != EMPTY) {
-        unsigned long long d = cnt16_at(cnt, t), b = d * (d - 1) / 2;
-        own += b;
-        if (PV && b) pv_add(s_hub, a, k, b);
-      }
+    for (uint32_t bits = occ[lane]; bits; bits &= bits - 1) {
+      const uint32_t t = lane * 32 + (__ffs(bits) - 1);
+      unsigned long long d = cnt16_at(cnt, t), b = d * (d - 1) / 2;
+      own += b;
+      if (PV && b) pv_add(s_hub, a, key[t], b);
     }
     own = warp_sum(own);
     if (lane == 0) {
@@ -432,6 +457,13 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
         }
         __syncwarp();
       }
+    }
+    __syncwarp();
+    // reset the entries this owner took (lane l: its 32 entries, its 16 count words)
+    for (uint32_t bits = occ[lane]; bits; bits &= bits - 1) key[lane * 32 + (__ffs(bits) - 1)] = EMPTY;
+    if (occ[lane]) {
+      for (uint32_t t = 0; t < 16; t++) cnt[lane * 16 + t] = 0;
+      occ[lane] = 0;
     }
     __syncwarp();
   }
