@@ -58,10 +58,10 @@ enum { ACC_GLOBAL = 0, ACC_OVF = 1, ACC_QMED = 2, ACC_QHEAVY = 3, ACC_NLIGHT = 4
 // Probe loops are bounded by the table size; running past it (impossible at
 // load <= 1/2 unless scratch is corrupt) records an error instead of spinning.
 
-constexpr uint32_t LIGHT_MAX = 512;   // wedges of a light first endpoint
+constexpr uint32_t LIGHT_MAX = 768;   // wedges of a light first endpoint
 constexpr int LW_THREADS = 512;
 constexpr int LW_WARPS = LW_THREADS / 32;
-constexpr int LW_CAP = 1024;          // per-warp table entries (>= 2 * LIGHT_MAX)
+constexpr int LW_CAP = 1024;          // per-warp table entries (> LIGHT_MAX: never full)
 constexpr int LW_LG = 10;
 constexpr uint32_t MED_MAX = 4096;
 constexpr int MB_THREADS = 512;
