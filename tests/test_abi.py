@@ -54,3 +54,28 @@ def test_package_does_not_import_the_oracle():
                     txt = f.read()
                 assert "import oracle" not in txt and "from oracle" not in txt, fn
                 assert "pb_oracle" not in txt, fn
+
+
+def test_error_paths_return_status_without_a_device():
+    """Calls that need no device reject bad arguments with PB_ERR_INVALID;
+    graph construction on a machine without a CUDA device returns an error
+    status (and a message) instead of aborting."""
+    import numpy as np
+    import torch
+    from paper_1907_08607_gb300 import build as b
+    import paper_1907_08607_gb300 as pb
+    lib = pb.load_library(b.build())
+    for code, name in pb.STATUS.items():
+        assert lib.pb_status_string(code).decode() == name
+    assert lib.pb_set_retrieval(None, 0) == 1
+    assert lib.pb_set_butterfly_aggregation(None, 0) == 1
+    assert lib.pb_graph_free(None) in (0, 1)
+    assert lib.pb_wedge_count(None, None) == 1
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    u = np.array([0, 1], np.uint32)
+    out = ctypes.c_void_p()
+    rc = lib.pb_graph_from_edges(2, 2, 2, ctypes.c_void_p(u.ctypes.data), ctypes.c_void_p(u.ctypes.data), 0, None,
+                                 ctypes.byref(out))
+    assert rc != 0 and out.value is None
+    assert lib.pb_last_error()
