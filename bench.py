@@ -343,10 +343,13 @@ def run_gb300(args):
         per_launch_ms = kp["ms"] / kp["records"]
         per_launch_bytes = BYTES_PER_WEDGE[args.outputs] * kp["wedges"] / kp["records"]
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+        traffic = measured_traffic(kern, kp["wedges"] / kp["records"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(kern, kp["wedges"] / kp["records"]), "kernel": kern,
-                "peak_source": peak_src,
+                "traffic": traffic, "kernel": kern, "peak_source": peak_src,
                 "launch_ms": per_launch_ms, "algorithmic_bytes_per_launch": per_launch_bytes}
+        if traffic:  # the DRAM bytes the kernel moves (ncu), over the same launch time
+            roof["traffic_gbs"] = traffic / (per_launch_ms / 1e3) / 1e9
+            roof["traffic_frac"] = roof["traffic_gbs"] / peak
 
     if rank != 0:
         if dist is not None:
