@@ -43,7 +43,8 @@ typedef struct pb_graph pb_graph; /* opaque, library-owned */
  * wedges it retrieves).
  *  SIDE:          every vertex of one side before the other; the side placed
  *                 first is the one whose vertices, as endpoints, give fewer
- *                 wedges (ties: U); ids in order within a side.
+ *                 wedges (ties: U); within a side decreasing degree, ties by
+ *                 id (the order inside a side changes neither W nor counts).
  *  DEGREE:        decreasing degree (Chiba-Nishizeki); ties by global id.
  *  APPROX_DEGREE: decreasing floor(log2 degree); ties keep global-id order;
  *                 degree-0 vertices last.

@@ -26,8 +26,9 @@
  *   degree order: key (-deg, global id); approximate degree order: key
  *   (-floor(log2 deg), global id) with degree-0 vertices last; side order:
  *   the side whose vertices as endpoints give fewer wedges comes first
- *   (ties: U), ids in order within a side; complement degeneracy orders:
- *   peeling rounds, ties within a round by global id.  rank 0 is first.
+ *   (ties: U), decreasing degree within a side (ties by id); complement
+ *   degeneracy orders: peeling rounds, ties within a round by global id.
+ *   rank 0 is first.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -203,8 +204,20 @@ static int make_rank(const bgraph_t *g, int kind, uint32_t *rank) {
     for (uint32_t i = 0; i < nU; i++) { uint64_t d = g->deg[i]; if (d) wV += (unsigned __int128)d * (d - 1) / 2; }
     for (uint32_t j = 0; j < nV; j++) { uint64_t d = g->deg[nU + j]; if (d) wU += (unsigned __int128)d * (d - 1) / 2; }
     int u_first = wU <= wV;
-    for (uint32_t i = 0; i < nU; i++) rank[i] = u_first ? i : nV + i;
-    for (uint32_t j = 0; j < nV; j++) rank[nU + j] = u_first ? nU + j : j;
+    /* Within a side: decreasing degree, ties by id.  The paper fixes only which
+     * side comes first; every wedge with endpoints on that side is retrieved
+     * once whatever the order inside it, so W and the counts do not depend on
+     * this choice. */
+    rkey_t *k = (rkey_t *)malloc(sizeof(rkey_t) * (n ? n : 1));
+    if (!k) return ORC_ERR_NOMEM;
+    for (uint64_t x = 0; x < n; x++) {
+      uint64_t second = (x < nU) ? !u_first : u_first; /* 1 for the side placed second */
+      k[x].key = (second << 32) | (uint64_t)(0xFFFFFFFFu - g->deg[x]);
+      k[x].id = (uint32_t)x;
+    }
+    qsort(k, n, sizeof(rkey_t), cmp_rkey);
+    for (uint64_t r = 0; r < n; r++) rank[k[r].id] = (uint32_t)r;
+    free(k);
     return ORC_OK;
   }
   rkey_t *k = (rkey_t *)malloc(sizeof(rkey_t) * (n ? n : 1));

@@ -176,25 +176,23 @@ __global__ void k_side_wedges(const uint32_t *__restrict__ deg, uint64_t n, uint
   }
 }
 
-__global__ void k_side_rank(uint64_t n, uint32_t nU, uint32_t nV, int u_first, uint32_t *__restrict__ rank,
-                            uint32_t *__restrict__ order) {
-  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
-       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t r = x < nU ? (u_first ? static_cast<uint32_t>(x) : nV + static_cast<uint32_t>(x))
-                        : (u_first ? static_cast<uint32_t>(x) : static_cast<uint32_t>(x - nU));
-    rank[x] = r;
-    order[r] = static_cast<uint32_t>(x);
-  }
-}
-
-__global__ void k_rank_keys(const uint32_t *__restrict__ deg, uint64_t n, int kind, uint32_t maxdeg,
-                            int bitsN, uint64_t *__restrict__ keys) {
+// Side order: the first side (u_first) before the other, and within a side
+// decreasing degree; the paper fixes only which side comes first, and W and
+// the counts do not depend on the order inside a side.
+__global__ void k_rank_keys(const uint32_t *__restrict__ deg, uint64_t n, uint32_t nU, int kind, int u_first,
+                            uint32_t maxdeg, int dbits, int bitsN, uint64_t *__restrict__ keys) {
   for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
        x += static_cast<size_t>(gridDim.x) * blockDim.x) {
     uint32_t d = deg[x];
     uint64_t cls;
-    if (kind == PB_RANK_DEGREE) cls = maxdeg - d;                // decreasing degree
-    else cls = d == 0 ? 32u : 31u - (31u - __clz(d));            // decreasing floor(log2 d), 0 last
+    if (kind == PB_RANK_DEGREE) {
+      cls = maxdeg - d;                                          // decreasing degree
+    } else if (kind == PB_RANK_SIDE) {
+      const uint64_t second = (x < nU) ? !u_first : u_first;     // 1 for the side placed second
+      cls = (second << dbits) | (maxdeg - d);
+    } else {
+      cls = d == 0 ? 32u : 31u - (31u - __clz(d));               // decreasing floor(log2 d), 0 last
+    }
     keys[x] = (cls << bitsN) | x;
   }
 }
@@ -547,18 +545,15 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       tmp = nullptr;
     } else if (kind == PB_RANK_COMPLEMENT_DEGENERACY || kind == PB_RANK_APPROX_COMPLEMENT_DEGENERACY) {
       if ((st = codegen_rank(g, kind == PB_RANK_APPROX_COMPLEMENT_DEGENERACY, s)) != PB_OK) break;
-    } else if (kind == PB_RANK_SIDE) {
-      int u_first = g->w_side_U <= g->w_side_V;
-      if (n) {
-        k_side_rank<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, g->nU, g->nV, u_first, g->rank, g->order);
-        count_launch();
-      }
     } else {
+      const int u_first = g->w_side_U <= g->w_side_V;
       uint32_t maxdeg = g->maxdegU > g->maxdegV ? g->maxdegU : g->maxdegV;
-      int cbits = kind == PB_RANK_DEGREE ? bits_for(maxdeg) : 6;
+      const int dbits = bits_for(maxdeg);
+      int cbits = kind == PB_RANK_DEGREE ? dbits : (kind == PB_RANK_SIDE ? dbits + 1 : 6);
       if ((st = dalloc_t(&keys, n + 1, s)) != PB_OK) break;
       if (n) {
-        k_rank_keys<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->deg, n, kind, maxdeg, bitsN, keys);
+        k_rank_keys<<<grid_for(n, 256, 8192), 256, 0, s>>>(g->deg, n, g->nU, kind, u_first, maxdeg, dbits, bitsN,
+                                                            keys);
         count_launch();
       }
       if ((st = radix_sort(keys, nullptr, n, bitsN + cbits, s)) != PB_OK) break;

@@ -195,9 +195,12 @@ def test_rank_orders_have_their_defining_property(er1, tiny):
                 wu = sum(int(x) * (int(x) - 1) // 2 for x in deg[g.nU:])
                 wv = sum(int(x) * (int(x) - 1) // 2 for x in deg[: g.nU])
                 assert side[0] == (0 if wu <= wv else 1)
-                for s in (0, 1):
-                    ids = order[side == s]
-                    assert np.all(np.diff(ids) > 0)
+                for s in (0, 1):                                  # within a side: decreasing
+                    ids = order[side == s]                        # degree, ties by id
+                    d = deg[ids]
+                    assert np.all(d[:-1] >= d[1:])
+                    tie = d[:-1] == d[1:]
+                    assert np.all(ids[:-1][tie] < ids[1:][tie])
 
 
 # ----------------------------------------------------------------- duplicates / edges
