@@ -170,6 +170,32 @@ def test_side_order_wedge_closed_form(er1, tiny):
         assert oracle.count(g.nU, g.nV, g.u, g.v, kind="side", per_edge=False).W == W
 
 
+def test_side_order_wedges_do_not_depend_on_the_order_inside_a_side(tiny):
+    """The order inside each side (a reading: the paper fixes only which side
+    comes first) changes neither W nor the counts: any side-first ranking with
+    a random order inside the sides retrieves the same wedges, checked against
+    brute force."""
+    for i, g in enumerate(tiny[:30]):
+        n = g.nU + g.nV
+        side = oracle.rank(g.nU, g.nV, g.u, g.v, "side")
+        u_first = g.nU > 0 and int(side[: g.nU].min()) == 0   # U holds rank 0
+        perm = random_rank(900 + i, n).astype(np.int64)
+        first = np.arange(g.nU) if u_first else np.arange(g.nU, n)
+        second = np.arange(g.nU, n) if u_first else np.arange(g.nU)
+        order = np.concatenate([first[np.argsort(perm[first], kind="stable")],
+                                second[np.argsort(perm[second], kind="stable")]])
+        rk = np.empty(n, np.uint32)
+        rk[order] = np.arange(n, dtype=np.uint32)
+        W = oracle.wedges(g.nU, g.nV, g.u, g.v, kind="side")
+        assert oracle.wedges(g.nU, g.nV, g.u, g.v, rank_of=rk) == W
+        assert brute.wedges(g.nU, g.nV, g.u, g.v, rk) == W
+        ref = oracle.count(g.nU, g.nV, g.u, g.v, kind="side")
+        c = oracle.count(g.nU, g.nV, g.u, g.v, rank_of=rk)
+        assert c.global_count == ref.global_count
+        np.testing.assert_array_equal(c.per_vertex, ref.per_vertex)
+        np.testing.assert_array_equal(c.per_edge, ref.per_edge)
+
+
 def test_rank_orders_have_their_defining_property(er1, tiny):
     for g in [er1] + tiny[:20]:
         n = g.nU + g.nV
