@@ -141,7 +141,7 @@ typedef struct {
  * host or device arrays of m uint32 each (on_device selects).  Duplicated
  * pairs collapse into one edge; per-edge outputs still have one entry per
  * input pair, in input order.  Returns PB_ERR_INVALID if u[k] >= nU or
- * v[k] >= nV for any k.  The graph is ranked with PB_RANK_SIDE until pb_rank
+ * v[k] >= nV for any k, or if nU + nV = 0.  The graph is ranked with PB_RANK_SIDE until pb_rank
  * is called; that ranking is computed on the first call that needs one (a
  * count, pb_wedge_count, pb_graph_info, ...), so pb_rank straight after this
  * call runs PREPROCESS once.  Calls without a stream argument that trigger it

@@ -227,6 +227,18 @@ def test_degenerate_inputs(pb):
     G = pb.Graph.from_edges(1, 1, np.zeros(1, np.uint32), np.zeros(1, np.uint32)).rank("degree")
     assert G.count_global() == 0 and G.wedges == 0
     G.free()
+    # one empty side, and isolated vertices only: no wedges, all counts zero
+    for nU, nV in [(0, 5), (5, 0), (1, 1)]:
+        G = pb.Graph.from_edges(nU, nV, e, e)
+        for kind in RANKS:
+            G.rank(kind)
+            assert G.wedges == 0 and G.count_global() == 0
+            U, V = G.count_vertex()
+            assert U.shape == (nU,) and V.shape == (nV,) and not U.any() and not V.any()
+        G.free()
+    with pytest.raises(pb.PBError) as ei:  # no vertices at all
+        pb.Graph.from_edges(0, 0, e, e)
+    assert ei.value.status == 1
     # invalid ids / rankings are rejected with PB_ERR_INVALID
     with pytest.raises(pb.PBError) as ei:
         pb.Graph.from_edges(2, 2, np.array([0, 2], np.uint32), np.array([0, 1], np.uint32))
