@@ -391,19 +391,41 @@ __global__ void k_arcs_out(const uint64_t *__restrict__ keys, const uint32_t *__
   }
 }
 
+// degp[x] = deg_x(x): the neighbours of x ranked above it.  One pass over the
+// canonical edges: each edge adds one to its lower-ranked endpoint (labels;
+// warp-aggregated, since edges come grouped by U endpoint).
+__global__ void k_degp_edges(const uint32_t *__restrict__ eu, const uint32_t *__restrict__ ev, uint64_t m,
+                             uint32_t nU, const uint32_t *__restrict__ rank, const uint32_t *__restrict__ label,
+                             uint32_t *__restrict__ degp) {
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t iters = (m + stride - 1) / stride;
+  for (size_t itn = 0; itn < iters; itn++) {  // uniform trip count: the whole warp reaches the match
+    const size_t e = start + itn * stride;
+    uint32_t t = 0xffffffffu;
+    if (e < m) {
+      const uint32_t a = eu[e], b = nU + ev[e];
+      t = rank[b] > rank[a] ? label[a] : label[b];
+    }
+    const uint32_t peers = __match_any_sync(FULL, t);
+    if (t != 0xffffffffu && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&degp[t], __popc(peers));
+  }
+}
+
 // cpos[s] = position of the list owner x in y's list (= deg_x(y), the number
 // of y's neighbours ranked above x, since lists are strictly decreasing in
-// rank); degp[x] = deg_x(x), the length of the prefix of x's list ranked above
-// x.  Neighbour ranks come from the sort keys, the owner's from lrank.
-// The same pass adds, for the lower-endpoint owner x, the wedges through
-// every neighbour of its prefix: wedges(x) = sum of cpos over the first
-// degp[x] slots of x (warp-aggregated atomics into wc).
-__global__ void k_cpos_degp(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                            uint64_t na, int bitsN, const uint32_t *__restrict__ off,
-                            const uint32_t *__restrict__ adj, const uint32_t *__restrict__ slotA,
-                            const uint32_t *__restrict__ slotB, const uint32_t *__restrict__ lrank,
-                            uint32_t *__restrict__ cpos, uint32_t *__restrict__ degp,
-                            unsigned long long *__restrict__ wc) {
+// rank).  The same pass counts the wedges of every owner in both directions
+// (warp-aggregated atomics):
+//   wc[x]  (x the lower-ranked endpoint, Algorithm 2): cpos over the first
+//          degp[x] slots of x;
+//   wcr[x] (x the higher-ranked endpoint): for every neighbour y (slot s),
+//          the entries of y's list ranked below both y and x.
+__global__ void k_cpos_wedges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                              uint64_t na, int bitsN, const uint32_t *__restrict__ off,
+                              const uint32_t *__restrict__ adj, const uint32_t *__restrict__ slotA,
+                              const uint32_t *__restrict__ slotB, const uint32_t *__restrict__ lrank,
+                              const uint32_t *__restrict__ degp, uint32_t *__restrict__ cpos,
+                              unsigned long long *__restrict__ wc, unsigned long long *__restrict__ wcr) {
   const uint64_t mask = (uint64_t(1) << bitsN) - 1;
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   const size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -412,53 +434,31 @@ __global__ void k_cpos_degp(const uint64_t *__restrict__ keys, const uint32_t *_
     const size_t s = start + itn * stride;
     const bool valid = s < na;
     uint32_t x = 0xffffffffu;
-    unsigned long long c = 0;
+    unsigned long long c = 0, cr = 0;
     if (valid) {
-      uint32_t a = vals[s];
-      uint32_t other = (a & 1u) ? slotA[a >> 1] : slotB[a >> 1];
-      const uint32_t cp = other - off[adj[s]];
+      const uint32_t a = vals[s], y = adj[s];
+      const uint32_t other = (a & 1u) ? slotA[a >> 1] : slotB[a >> 1];
+      const uint32_t oy = off[y], cp = other - oy;
       cpos[s] = cp;
       x = static_cast<uint32_t>(keys[s] >> bitsN);
-      uint32_t rx = lrank[x];
-      uint32_t ry = static_cast<uint32_t>(mask - (keys[s] & mask));
-      if (ry > rx) {
-        c = cp;
-        bool last = s + 1 == off[x + 1];
-        if (!last) last = static_cast<uint32_t>(mask - (keys[s + 1] & mask)) < rx;
-        if (last) degp[x] = static_cast<uint32_t>(s + 1 - off[x]);
-      }
+      const uint32_t rx = lrank[x], ry = static_cast<uint32_t>(mask - (keys[s] & mask));
+      if (ry > rx) c = cp;
+      const uint32_t dy = off[y + 1] - oy;
+      uint32_t st = degp[y];
+      if (cp + 1 > st) st = cp + 1;
+      cr = dy > st ? dy - st : 0;
     }
     const uint32_t peers = __match_any_sync(FULL, x);
-    unsigned long long tot = 0;
-    for (uint32_t q = peers; q; q &= q - 1) tot += __shfl_sync(peers, c, __ffs(q) - 1);
-    if (valid && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1) && tot) atomicAdd(&wc[x], tot);
-  }
-}
-
-// Wedges owned by their higher-ranked endpoint x: for each neighbour y (slot
-// s of x), the entries of y's list ranked below both y and x.
-__global__ void k_wedges_rev(const uint64_t *__restrict__ keys, uint64_t na, int bitsN,
-                             const uint32_t *__restrict__ off, const uint32_t *__restrict__ degp,
-                             const uint32_t *__restrict__ adj, const uint32_t *__restrict__ cpos,
-                             unsigned long long *__restrict__ wc) {
-  size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-  size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  size_t iters = (na + stride - 1) / stride;
-  for (size_t it = 0; it < iters; it++) {
-    size_t s = start + it * stride;
-    bool valid = s < na;
-    uint32_t x = valid ? static_cast<uint32_t>(keys[s] >> bitsN) : 0xffffffffu;
-    unsigned long long c = 0;
-    if (valid) {
-      uint32_t y = adj[s], p = cpos[s], dy = off[y + 1] - off[y], st = degp[y];
-      if (p + 1 > st) st = p + 1;
-      c = dy > st ? dy - st : 0;
+    unsigned long long tot = 0, totr = 0;
+    for (uint32_t q = peers; q; q &= q - 1) {
+      const int l = __ffs(q) - 1;
+      tot += __shfl_sync(peers, c, l);
+      totr += __shfl_sync(peers, cr, l);
     }
-    uint32_t peers = __match_any_sync(FULL, x);
-    uint32_t leader = __ffs(peers) - 1;
-    unsigned long long tot = 0;
-    for (uint32_t q = peers; q; q &= q - 1) tot += __shfl_sync(peers, c, __ffs(q) - 1);
-    if (valid && lane_id() == leader && tot) atomicAdd(&wc[x], tot);
+    if (valid && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
+      if (tot) atomicAdd(&wc[x], tot);
+      if (totr) atomicAdd(&wcr[x], totr);
+    }
   }
 }
 
@@ -582,8 +582,13 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
     dfree(tmp, s);
     tmp = nullptr;
     if (cudaMemsetAsync(g->degp, 0, (n + 1) * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-    if ((st = dalloc_t(&wc, n + 1, s)) != PB_OK) break;
-    if (cudaMemsetAsync(wc, 0, (n + 1) * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    if (m > 0) {
+      k_degp_edges<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, g->rank, g->label, g->degp);
+      count_launch();
+    }
+    if ((st = dalloc_t(&wc, 2 * (n + 1), s)) != PB_OK) break;  // both directions
+    if (cudaMemsetAsync(wc, 0, 2 * (n + 1) * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+    unsigned long long *wcr = wc + (n + 1);
     if (na > 0) {
       // ---- 3. arcs sorted by (source, decreasing neighbour)
       if ((st = dalloc_t(&keys, na, s)) != PB_OK) break;
@@ -594,9 +599,9 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       if ((st = radix_sort(keys, vals, na, 2 * bitsN, s)) != PB_OK) break;
       k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, rlab, g->adj, g->slotA, g->slotB);
       count_launch();
-      // ---- 4. (same pass) wedges per first endpoint, then the work split prefix
-      k_cpos_degp<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->off, g->adj, g->slotA,
-                                                           g->slotB, lrank, g->cpos, g->degp, wc);
+      // ---- 4. (same pass) wedges per owner in both directions, then the work split prefixes
+      k_cpos_wedges<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, g->off, g->adj, g->slotA,
+                                                             g->slotB, lrank, g->degp, g->cpos, wc, wcr);
       count_launch();
     }
     if ((st = scan_u64(reinterpret_cast<uint64_t *>(wc), g->wpre, n, s)) != PB_OK) break;
@@ -606,14 +611,9 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       count_launch();
     }
     // the same wedges counted at their higher-ranked endpoint
-    if (cudaMemsetAsync(wc, 0, (n + 1) * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-    if (na > 0) {
-      k_wedges_rev<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, na, bitsN, g->off, g->degp, g->adj, g->cpos, wc);
-      count_launch();
-    }
-    if ((st = scan_u64(reinterpret_cast<uint64_t *>(wc), g->wpre_rev, n, s)) != PB_OK) break;
+    if ((st = scan_u64(reinterpret_cast<uint64_t *>(wcr), g->wpre_rev, n, s)) != PB_OK) break;
     if (n) {
-      k_max_u64<<<grid_for(n, 256, 2048), 256, 0, s>>>(wc, n, acc + 1);
+      k_max_u64<<<grid_for(n, 256, 2048), 256, 0, s>>>(wcr, n, acc + 1);
       count_launch();
     }
     uint64_t hW = 0, hWr = 0;
