@@ -68,9 +68,11 @@ typedef enum {
  *  HASH:  open-addressing hash tables keyed by the second endpoint, one per
  *         first endpoint: in shared memory for first endpoints with few
  *         wedges, in device memory (atomic-add combining) for heavy ones.
- *  HIST:  as HASH for light first endpoints; heavy (low-rank) first endpoints
- *         count their wedges in a dense histogram over all second endpoints,
- *         shared by a thread-block cluster.
+ *  HIST:  as HASH for first endpoints with few wedges; heavy ones count
+ *         their wedges in a dense histogram over the range of labels their
+ *         second endpoints can take, the most frequent part of it in shared
+ *         memory; the largest ones share a histogram among a thread-block
+ *         cluster.
  *  BATCH: dense arrays over the range of second endpoints, one per
  *         concurrently processed first endpoint, as many as the scratch
  *         budget holds (simple batching), one block each; first endpoints are
@@ -94,7 +96,8 @@ typedef enum {
  *        its higher-ranked endpoint by the lower one.  Owners then have far
  *        fewer wedges each, and the grouping keys concentrate on the few
  *        lowest-ranked (highest-degree) vertices.
- *  AUTO: HIGH.  Counts and the wedge total W are the same either way. */
+ *  AUTO: HIGH unless its largest owner holds more wedges than LOW's.
+ *  Counts and the wedge total W are the same either way. */
 typedef enum {
   PB_RETRIEVE_LOW = 0,
   PB_RETRIEVE_HIGH = 1,
