@@ -10,9 +10,12 @@ One step = the whole counting path over one synthetic graph:
 Metric: wedges aggregated per second, W / step time, where W is the exact
 number of wedges the ranking retrieves (Algorithm 2).  Counts are exact uint64.
 
-Default workload: Chung-Lu bipartite graph |U|=1M, |V|=4M, m=50M distinct
-edges, expected-degree exponents 2.1 (U) / 2.5 (V), expected degree capped at
-1e5, degree ranking, automatic aggregation.
+Default workload: the largest single-GPU configuration, a Chung-Lu
+bipartite graph |U|=20M, |V|=60M, m=300M distinct edges, expected-degree
+exponent 2.0 on both sides (capped at 1e5), degree ranking, exact global and
+per-edge counts, batch aggregation (simple batching) within a 16 GiB scratch
+budget.  `--workload cl2` selects the 1M x 4M graph (all outputs, automatic
+aggregation).
 
 Multi-GPU (torchrun): every rank counts its own replica of the workload (the
 path has no exchange step), so per-GPU work is fixed: weak scaling, value =
@@ -38,26 +41,44 @@ sys.path.insert(0, ROOT)
 METRIC = "wedges aggregated/sec and % HBM roofline, exact counts; batched/served p50/p99 vs plain"
 UNIT = "wedges/s"
 
+# Each workload with the counting configuration it is measured in (ranking,
+# aggregation, outputs, scratch budget); command-line options override them.
 WORKLOADS = {
-    "er1": dict(desc="ER |U|=2000 |V|=3000 m=2e4", idx=1),
-    "cl2": dict(desc="Chung-Lu |U|=1M |V|=4M m=5e7, exponents 2.1/2.5, cap 1e5", idx=2),
-    "cl3": dict(desc="Chung-Lu |U|=20M |V|=60M m=3e8, exponents 2.0/2.0, cap 1e5", idx=3),
+    "er1": dict(desc="ER |U|=2000 |V|=3000 m=2e4", idx=1, agg="hash", outputs="vertex", scratch=0),
+    "cl2": dict(desc="Chung-Lu |U|=1M |V|=4M m=5e7, exponents 2.1/2.5, cap 1e5", idx=2, agg="auto",
+                outputs="all", scratch=0),
+    "cl3": dict(desc="Chung-Lu |U|=20M |V|=60M m=3e8, exponents 2.0/2.0, cap 1e5", idx=3, agg="batch",
+                outputs="edge", scratch=16 << 30),
     # quarter-scale copy of cl2 for profiler captures (a few GB on the device)
-    "cl2s": dict(desc="Chung-Lu |U|=250k |V|=1M m=1.25e7, exponents 2.1/2.5, cap 1e5", idx=-2),
+    "cl2s": dict(desc="Chung-Lu |U|=250k |V|=1M m=1.25e7, exponents 2.1/2.5, cap 1e5", idx=-2, agg="auto",
+                 outputs="all", scratch=0),
+    # 1/16-scale copy of cl3 for profiler captures (same recipe and counting configuration)
+    "cl3s": dict(desc="Chung-Lu |U|=1.25M |V|=3.75M m=1.875e7, exponents 2.0/2.0, cap 1e5", idx=-3, agg="batch",
+                 outputs="edge", scratch=1 << 30),
 }
-# Bounded CPU sample of each workload for the oracle: the same generator
-# recipe at a reduced scale.
+# CPU samples of each workload for the oracle: the same generator recipe at a
+# reduced scale.  "baseline" is the cpu_baseline of the GPU line (about 10-30 s
+# of oracle time on the host cores); "step" is one step of the reference arm,
+# small enough that warm-up plus timed steps end within a few minutes.
 SAMPLES = {
-    "er1": dict(kind="er", nU=2000, nV=3000, m=20000),
-    "cl2": dict(kind="cl", nU=200_000, nV=800_000, m=10_000_000, gu=2.1, gv=2.5, cap=1e5),
-    "cl3": dict(kind="cl", nU=800_000, nV=2_400_000, m=12_000_000, gu=2.0, gv=2.0, cap=1e5),
-    "cl2s": dict(kind="cl", nU=200_000, nV=800_000, m=10_000_000, gu=2.1, gv=2.5, cap=1e5),
+    "er1": dict(baseline=dict(kind="er", nU=2000, nV=3000, m=20000),
+                step=dict(kind="er", nU=2000, nV=3000, m=20000)),
+    "cl2": dict(baseline=dict(kind="cl", nU=400_000, nV=1_600_000, m=20_000_000, gu=2.1, gv=2.5, cap=1e5),
+                step=dict(kind="cl", nU=200_000, nV=800_000, m=10_000_000, gu=2.1, gv=2.5, cap=1e5)),
+    "cl3": dict(baseline=dict(kind="cl", nU=1_200_000, nV=3_600_000, m=18_000_000, gu=2.0, gv=2.0, cap=1e5),
+                step=dict(kind="cl", nU=400_000, nV=1_200_000, m=6_000_000, gu=2.0, gv=2.0, cap=1e5)),
+    "cl2s": dict(baseline=dict(kind="cl", nU=200_000, nV=800_000, m=10_000_000, gu=2.1, gv=2.5, cap=1e5),
+                 step=dict(kind="cl", nU=100_000, nV=400_000, m=5_000_000, gu=2.1, gv=2.5, cap=1e5)),
+    "cl3s": dict(baseline=dict(kind="cl", nU=1_200_000, nV=3_600_000, m=18_000_000, gu=2.0, gv=2.0, cap=1e5),
+                 step=dict(kind="cl", nU=400_000, nV=1_200_000, m=6_000_000, gu=2.0, gv=2.0, cap=1e5)),
 }
 
 # Algorithmic bytes per wedge of a pass producing global, per-vertex and
 # per-edge counts: 4 B to read the second endpoint, and an 8 B read + 8 B write
 # of the per-edge counter it updates ("streaming, no reuse" model).
-BYTES_PER_WEDGE = {"all": 20, "global": 4, "vertex": 8}
+BYTES_PER_WEDGE = {"all": 20, "edge": 20, "global": 4, "vertex": 8}
+OUTPUT_DESC = {"all": "global+per-vertex+per-edge", "edge": "global+per-edge", "global": "global",
+               "vertex": "global+per-vertex"}
 
 
 def parse():
@@ -70,18 +91,31 @@ def parse():
                     help="plain: one graph per step (default); batched: 1,024 graphs in one CUDA-graph launch "
                          "vs one launch per graph; serving: Poisson request stream")
     ap.add_argument("--graphs", type=int, default=1024)
-    ap.add_argument("--workload", default="cl2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cl3", choices=sorted(WORKLOADS))
     ap.add_argument("--rank", default="degree", choices=["side", "degree", "approx_degree", "complement_degeneracy",
                                                         "approx_complement_degeneracy"])
-    ap.add_argument("--agg", default="auto", choices=["sort", "hash", "hist", "batch", "auto"])
-    ap.add_argument("--outputs", default="all", choices=["all", "global", "vertex"])
+    ap.add_argument("--agg", default=None, choices=["sort", "hash", "hist", "batch", "auto"],
+                    help="wedge aggregation (default: the workload's)")
+    ap.add_argument("--outputs", default=None, choices=["all", "edge", "global", "vertex"],
+                    help="counts produced (default: the workload's)")
+    ap.add_argument("--scratch-gib", type=float, default=None,
+                    help="aggregation scratch budget in GiB (default: the workload's; 0 = library default)")
+    ap.add_argument("--cpu-sample", default="bounded", choices=["bounded", "full"],
+                    help="cpu_baseline on the bounded sample (default) or on the full workload graph")
     ap.add_argument("--retrieval", default="auto", choices=["low", "high", "auto"])
     ap.add_argument("--butterfly", default="atomic", choices=["atomic", "sort"],
                     help="butterfly aggregation: atomic adds or sort re-aggregation (needs --agg sort)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.agg is None:
+        args.agg = wl["agg"]
+    if args.outputs is None:
+        args.outputs = wl["outputs"]
+    args.scratch = wl["scratch"] if args.scratch_gib is None else int(args.scratch_gib * (1 << 30))
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -176,23 +210,35 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(workload: str, nthreads: int | None = None) -> dict:
-    """The oracle as it stands, on a bounded sample of the workload."""
-    import oracle
+def _sample_graph(workload: str, which: str):
     import synth
-    sp = SAMPLES[workload]
+    if which == "full":
+        return synth.workload(WORKLOADS[workload]["idx"]), f"the full {WORKLOADS[workload]['desc']} graph"
+    sp = SAMPLES[workload][which]
     seed = synth.SEED_BASE + 100 + WORKLOADS[workload]["idx"]
     if sp["kind"] == "er":
         g = synth.er_graph(seed, sp["nU"], sp["nV"], sp["m"])
     else:
         g = synth.chung_lu_graph(seed, sp["nU"], sp["nV"], sp["m"], sp["gu"], sp["gv"], cap_u=sp["cap"],
                                  cap_v=sp["cap"])
+    return g, f"{sp['kind']} |U|={sp['nU']} |V|={sp['nV']} m={sp['m']} (same recipe, reduced scale)"
+
+
+def cpu_baseline(workload: str, nthreads: int | None = None, which: str = "baseline", outputs: str | None = None,
+                 rank: str = "degree") -> dict:
+    """The oracle as it stands, on a sample of the workload ("baseline":
+    bounded sample for the GPU line; "step": one reference-arm step; "full":
+    the workload graph itself).  Dedupe, PREPROCESS and counting are timed."""
+    import oracle
+    outputs = outputs or WORKLOADS[workload]["outputs"]
+    g, gdesc = _sample_graph(workload, which)
     threads = nthreads or oracle.threads()
+    pv = outputs in ("all", "vertex")
+    pe = outputs in ("all", "edge")
     t0 = time.perf_counter()
-    c = oracle.count(g.nU, g.nV, g.u, g.v, kind="degree", per_vertex=True, per_edge=True, nthreads=threads)
+    c = oracle.count(g.nU, g.nV, g.u, g.v, kind=rank, per_vertex=pv, per_edge=pe, nthreads=threads)
     dt = time.perf_counter() - t0
-    desc = (f"{sp['kind']} |U|={sp['nU']} |V|={sp['nV']} m={sp['m']} (same recipe, reduced scale), degree "
-            f"ranking, global+per-vertex+per-edge, dedupe+preprocess+count timed")
+    desc = f"{gdesc}, {rank} ranking, {OUTPUT_DESC[outputs]}, dedupe+preprocess+count timed, W={c.W}"
     return {"value": c.W / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
             "seconds": dt, "W": c.W}
 
@@ -202,17 +248,18 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        cpu_baseline(args.workload)
+        cpu_baseline(args.workload, which="step", outputs=args.outputs, rank=args.rank)
     vals, secs = [], []
     for _ in range(args.steps):
-        r = cpu_baseline(args.workload)
+        r = cpu_baseline(args.workload, which="step", outputs=args.outputs, rank=args.rank)
         vals.append(r["value"])
         secs.append(r["seconds"])
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": r["sample"], "rank": "degree"},
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": r["sample"], "rank": args.rank,
+                       "outputs": OUTPUT_DESC[args.outputs]},
             "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": value,
                              "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -244,14 +291,20 @@ def run_gb300(args):
     # CPU baseline first (host threads only, before heavy GPU work).
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload)
+        cpu = cpu_baseline(args.workload, which="baseline" if args.cpu_sample == "bounded" else "full",
+                           outputs=args.outputs, rank=args.rank)
 
     g = synth.workload(WORKLOADS[args.workload]["idx"])
     du = torch.from_numpy(g.u.view(np.int32)).to(dev)
     dv = torch.from_numpy(g.v.view(np.int32)).to(dev)
-    outs = {"U": torch.empty(g.nU, dtype=torch.int64, device=dev),
-            "V": torch.empty(g.nV, dtype=torch.int64, device=dev),
-            "E": torch.empty(g.m, dtype=torch.int64, device=dev)}
+    want_v = args.outputs in ("all", "vertex")
+    want_e = args.outputs in ("all", "edge")
+    outs = {}
+    if want_v:
+        outs["U"] = torch.empty(g.nU, dtype=torch.int64, device=dev)
+        outs["V"] = torch.empty(g.nV, dtype=torch.int64, device=dev)
+    if want_e:
+        outs["E"] = torch.empty(g.m, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
 
     state = {}
@@ -260,8 +313,8 @@ def run_gb300(args):
         G = pb.Graph.from_edges(g.nU, g.nV, du, dv)
         G.rank(args.rank)
         G.set_retrieval(args.retrieval).set_butterfly_aggregation(args.butterfly)
-        c = G.count_all(args.agg, on_device=True, out=outs, vertex=args.outputs != "global",
-                        edge=args.outputs == "all")
+        c = G.count_all(args.agg, scratch_bytes=args.scratch, on_device=True, out=outs, vertex=want_v,
+                        edge=want_e)
         state["W"] = G.wedges
         state["global"] = c.global_count
         G.free()
@@ -303,15 +356,19 @@ def run_gb300(args):
     if not args.no_e2e:
         hu = torch.from_numpy(g.u.view(np.int32)).pin_memory()
         hv = torch.from_numpy(g.v.view(np.int32)).pin_memory()
-        hout = {"U": torch.empty(g.nU, dtype=torch.int64).pin_memory(),
-                "V": torch.empty(g.nV, dtype=torch.int64).pin_memory(),
-                "E": torch.empty(g.m, dtype=torch.int64).pin_memory()}
+        hout = {}
+        if want_v:
+            hout["U"] = torch.empty(g.nU, dtype=torch.int64).pin_memory()
+            hout["V"] = torch.empty(g.nV, dtype=torch.int64).pin_memory()
+        if want_e:
+            hout["E"] = torch.empty(g.m, dtype=torch.int64).pin_memory()
 
         def step_host():
             G = pb.Graph.from_edges(g.nU, g.nV, hu, hv)
             G.rank(args.rank)
             G.set_retrieval(args.retrieval).set_butterfly_aggregation(args.butterfly)
-            G.count_all(args.agg, on_device=False, out=hout)
+            G.count_all(args.agg, scratch_bytes=args.scratch, on_device=False, out=hout, vertex=want_v,
+                        edge=want_e)
             G.free()
 
         for _ in range(max(3, args.warmup)):
@@ -331,7 +388,8 @@ def run_gb300(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
         e2e = {"value": world * W / (ems / args.steps / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * g.m, "d2h_bytes_per_step": 8 * (g.nU + g.nV + g.m) + 8,
+               "h2d_bytes_per_step": 8 * g.m,
+               "d2h_bytes_per_step": 8 * ((g.nU + g.nV if want_v else 0) + (g.m if want_e else 0)) + 8,
                "ms_per_step": ems / args.steps}
 
     # ---- roofline of the dominant kernel (CUDA events inside the library)
@@ -361,10 +419,11 @@ def run_gb300(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "rank": args.rank, "agg": args.agg,
+                   "scratch_bytes": args.scratch or "library default (16 GiB)",
                    "retrieval": args.retrieval, "butterfly_aggregation": args.butterfly,
-                   "outputs": {"all": "global+per-vertex+per-edge", "global": "global",
-                               "vertex": "global+per-vertex"}[args.outputs], "W": W, "butterflies": state["global"],
-                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (400 MB edge list)"},
+                   "outputs": OUTPUT_DESC[args.outputs], "W": W, "butterflies": state["global"],
+                   "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 ({8 * g.m / 1e6:.0f} MB edge list)"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -164,6 +164,9 @@ def workload(idx: int) -> Graph:
     if idx == -2:  # quarter-scale copy of workload 2 (profiling)
         return chung_lu_graph(seed, 250_000, 1_000_000, 12_500_000, 2.1, 2.5,
                               name="cl_250kx1M_m1.25e7")
+    if idx == -3:  # 1/16-scale copy of workload 3 (profiling)
+        return chung_lu_graph(seed, 1_250_000, 3_750_000, 18_750_000, 2.0, 2.0,
+                              name="cl_1.25Mx3.75M_m1.875e7")
     raise KeyError(idx)
 
 

@@ -52,13 +52,27 @@ def test_clock_summary_reads_samples_and_reasons(bench):
 
 def test_model_bytes_per_wedge(bench):
     # 4 B second endpoint; + 4 B per-vertex traffic; + 8 B read and 8 B write of the edge counter
-    assert bench.BYTES_PER_WEDGE == {"all": 20, "global": 4, "vertex": 8}
+    assert bench.BYTES_PER_WEDGE == {"all": 20, "edge": 20, "global": 4, "vertex": 8}
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration(bench, monkeypatch):
+    """With no options the bench counts the 20M x 60M graph, per-edge, with
+    batch aggregation inside a 16 GiB scratch budget."""
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.workload == "cl3" and a.agg == "batch" and a.outputs == "edge" and a.scratch == 16 << 30
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "cl2", "--agg", "hash", "--scratch-gib", "2"])
+    a = bench.parse()
+    assert a.agg == "hash" and a.outputs == "all" and a.scratch == 2 << 30
 
 
 def test_cpu_baseline_times_the_oracle_on_a_bounded_sample(bench):
     r = bench.cpu_baseline("er1", nthreads=2)
     assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0 and r["W"] > 0
-    assert "er" in r["sample"]
+    assert "er" in r["sample"] and f"W={r['W']}" in r["sample"]
+    for wl, sp in bench.SAMPLES.items():   # every sample is the workload's recipe at a smaller scale
+        assert sp["step"]["m"] <= sp["baseline"]["m"]
 
 
 def test_status_codes_raise_with_the_library_message():

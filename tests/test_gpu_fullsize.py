@@ -94,15 +94,40 @@ def _digest(a):
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
 
 
-def test_cl3_batch_16gib_matches_oracle_digests_invariants_and_samples(pb):
-    """Complete oracle outputs on this workload are stored as SHA-256 digests
-    (tests/golden/cl3_oracle.json, written by tests/golden/make_cl3_oracle.py
-    from oracle.count); the GPU's per-vertex and per-edge arrays must hash to
-    the same values, and W and the global count must be equal."""
+@pytest.fixture(scope="module")
+def cl3():
     with open(os.path.join(os.path.dirname(__file__), "golden", "cl3_oracle.json")) as f:
         gold = json.load(f)
     g = synth.workload(3)
     assert (g.nU, g.nV, g.m) == (gold["nU"], gold["nV"], gold["m"])
+    return g, gold
+
+
+def test_cl3_bench_configuration_matches_oracle_digest(pb, cl3):
+    """The launch configuration bench.py times by default: device-resident
+    edge list, degree ranking, global + per-edge counts, batch aggregation
+    within 16 GiB; the per-edge array must hash to the oracle's digest."""
+    import torch
+    g, gold = cl3
+    du = torch.from_numpy(g.u.view(np.int32)).cuda()
+    dv = torch.from_numpy(g.v.view(np.int32)).cuda()
+    for _ in range(2):  # a second count on a fresh graph reuses the memory pool
+        G = pb.Graph.from_edges(g.nU, g.nV, du, dv).rank("degree")
+        assert G.wedges == gold["W"]
+        c = G.count_all("batch", scratch_bytes=16 << 30, vertex=False, edge=True, on_device=True)
+        G.free()
+        assert c.global_count == gold["global"]
+        assert _digest(c.per_edge.cpu().numpy().view(np.uint64)) == gold["per_edge_sha256"]
+    del du, dv, c
+    torch.cuda.empty_cache()
+
+
+def test_cl3_batch_16gib_matches_oracle_digests_invariants_and_samples(pb, cl3):
+    """Complete oracle outputs on this workload are stored as SHA-256 digests
+    (tests/golden/cl3_oracle.json, written by tests/golden/make_cl3_oracle.py
+    from oracle.count); the GPU's per-vertex and per-edge arrays must hash to
+    the same values, and W and the global count must be equal."""
+    g, gold = cl3
     G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
     assert G.info().m == g.m
     assert G.wedges == gold["W"]
