@@ -227,8 +227,10 @@ pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info);
 /* Sparsification for approximate total counts (Sec. "Approximate counting").
  *  EDGE:  keep each edge with probability p; the total butterfly count of the
  *         kept graph divided by p^4 is an unbiased estimate of the total.
- *  COLOR: colourful sparsification: each vertex gets one of ceil(1/p) colours,
- *         edges whose two endpoints share a colour are kept; divide by p^3.
+ *  COLOR: colourful sparsification: each vertex gets one of c = ceil(1/p)
+ *         colours, edges whose two endpoints share a colour are kept; a
+ *         butterfly survives with probability c^-3 (p^3 when 1/p is an
+ *         integer), so the kept count times c^3 is unbiased.
  * Decisions hash the pair (u, v) or the vertex (SplitMix64's output function,
  * seeded), so duplicate pairs share one decision and results are
  * reproducible.  Writes the kept pairs, in input order, to out_u / out_v
@@ -238,6 +240,21 @@ typedef enum { PB_SPARSIFY_EDGE = 0, PB_SPARSIFY_COLOR = 1 } pb_sparsify_kind;
 pb_status pb_sparsify(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v,
                       int on_device, pb_sparsify_kind kind, double p, uint64_t seed, uint32_t *out_u,
                       uint32_t *out_v, uint64_t *out_m, void *stream);
+
+/* Approximate total butterfly count (Sec. "Approximate counting"): the m
+ * pairs (host or device, on_device selects) are sparsified on the device as
+ * pb_sparsify does, the kept graph is built, ranked with `rank` and counted
+ * exactly with aggregation `agg` (scratch_bytes as for pb_count_global), and
+ * the device scales the exact count: by p^-4 (EDGE) or ceil(1/p)^3 (COLOR).
+ * *estimate (host) receives the estimate; *kept_count the exact butterfly
+ * count of the kept graph and *kept_edges the number of kept input pairs
+ * (either may be NULL).  PB_ERR_INVALID for p outside (0, 1], an unknown kind
+ * or out-of-range ids; all intermediate graphs and buffers are released
+ * before the call returns. */
+pb_status pb_count_approx(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *u, const uint32_t *v,
+                          int on_device, pb_sparsify_kind kind, double p, uint64_t seed, pb_rank_kind rank,
+                          pb_agg agg, uint64_t scratch_bytes, double *estimate, uint64_t *kept_count,
+                          uint64_t *kept_edges, void *stream);
 
 /* Autotuner: a plan from the graph's degree and wedge statistics.
  *  f_side = (W_side - W_rank) / W_side, W_side the wedges of side order (the
@@ -280,6 +297,16 @@ pb_status pb_batch_vertex(const pb_batch *b, uint32_t i, uint64_t *out_U, uint64
 pb_status pb_batch_wedges(const pb_batch *b, uint64_t *W);
 pb_status pb_batch_free(pb_batch *b);
 
+/* Copies the graph's PREPROCESS output (Algorithm 1) -- the layout that
+ * pb_count_noalloc takes -- into caller-owned buffers (host or device, as
+ * out_on_device selects; any may be NULL): off[n + 1] CSR offsets by label,
+ * adj[2m] neighbour labels in decreasing rank order, cpos[2m] (deg_x(y) for
+ * the entry holding y in x's list), degp[n] (deg_x(x)), and label_of[n], the
+ * label of every global id.  Ranks the graph by side order first if it has
+ * no ranking. */
+pb_status pb_graph_layout(const pb_graph *g, uint32_t *off, uint32_t *adj, uint32_t *cpos, uint32_t *degp,
+                          uint32_t *label_of, int out_on_device, void *stream);
+
 /* Releases the graph and every device buffer it holds.  NULL is accepted. */
 pb_status pb_graph_free(pb_graph *g);
 
@@ -305,14 +332,31 @@ pb_status pb_graph_free(pb_graph *g);
  * of more than 16,777,184 vertices does not fit and is rejected with
  * PB_ERR_INVALID.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array and leaves its
+ * call before any stream capture.  `stream` must belong to the current device
+ * (PB_ERR_INVALID otherwise).  Every call shares the array and leaves its
  * contents behind; the call clears what must start at zero.  Calls whose
  * device work overlaps (other streams, other threads) race on the array and
- * must be serialised by the caller.  Returns after the stream has completed
- * the work; PB_ERR_OVERFLOW if the global count exceeds 2^64. */
+ * must be serialised by the caller.
+ *
+ * The layout is checked on the device before it is used (offsets start at 0
+ * and never decrease, neighbour labels lie below n on the other side, no
+ * deg_x(y) or deg_x(x) entry exceeds the degree): a violation returns
+ * PB_ERR_INVALID and writes nothing but the cleared outputs.  off[n] must be
+ * the length of adj and cpos.  PB_ERR_OVERFLOW if the global count, or any
+ * partial sum of it, exceeds 2^64 - 1; no per-vertex count can exceed the
+ * global count, so this also covers out_pv.  Like every entry point, the call
+ * returns after its stream has completed the work. */
 pb_status pb_count_noalloc(uint64_t n, uint32_t nU, const uint32_t *off, const uint32_t *adj,
                            const uint32_t *cpos, const uint32_t *degp, uint64_t *out_global,
                            uint64_t *out_pv, void *stream);
+
+/* Measurement support, not part of the counting path: the current device's
+ * throughput of 64-bit atomic adds whose result is unused (performed in L2),
+ * in operations per second, over a 64 MiB array of counters.  scattered = 0:
+ * the 32 lanes of a warp add to 32 consecutive counters (the per-edge counter
+ * pattern); scattered != 0: every lane adds to a hashed counter (the
+ * per-vertex pattern).  Allocates and frees 64 MiB; takes a few ms. */
+pb_status pb_calibrate_atomics(int scattered, double *ops_per_s, void *stream);
 
 /* Number of device kernels the library has launched in this process (all
  * graphs, all devices); used to report launch counts. */

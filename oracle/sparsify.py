@@ -3,8 +3,10 @@
 
 Edge sparsification keeps each edge with probability p and divides the count
 of the kept graph by p^4; colourful sparsification colours every vertex with
-one of ceil(1/p) colours, keeps the edges whose endpoints share a colour and
-divides by p^3.  Each decision is a uniform draw from SplitMix64's output
+one of c = ceil(1/p) colours and keeps the edges whose endpoints share a
+colour.  A butterfly then survives when its other three vertices draw the
+first one's colour, with probability c^-3 -- the paper's p^3 when 1/p is an
+integer -- so the kept count is multiplied by c^3.  Each decision is a uniform draw from SplitMix64's output
 function (Steele, Lea & Flood, OOPSLA 2014) applied to the edge or vertex:
 h = mix(mix(seed ^ a * 0x9E3779B97F4A7C15) + b), U = (h >> 11) * 2^-53, with
 (a, b) = (u, v) for an edge and (global id, 0x5BD1E995) for a colour.
@@ -48,5 +50,5 @@ def keep_mask(nU: int, u, v, kind: str, p: float, seed: int) -> np.ndarray:
 def sparsify(nU: int, nV: int, u, v, kind: str, p: float, seed: int):
     """Kept pairs in input order, and the estimator's scale factor."""
     k = keep_mask(nU, u, v, kind, p, seed)
-    scale = 1.0 / p ** 4 if kind == "edge" else 1.0 / p ** 3
+    scale = 1.0 / p ** 4 if kind == "edge" else float(math.ceil(1.0 / p)) ** 3
     return np.asarray(u)[k].astype(np.uint32), np.asarray(v)[k].astype(np.uint32), scale

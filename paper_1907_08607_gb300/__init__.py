@@ -39,7 +39,8 @@ ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ran
                "pb_profile_enable", "pb_profile_reset", "pb_profile_read", "pb_count_noalloc",
                "pb_set_retrieval", "pb_count_owner_range", "pb_wedge_prefix", "pb_sparsify", "pb_autotune",
                "pb_batch_create", "pb_batch_run", "pb_batch_globals", "pb_batch_vertex", "pb_batch_wedges",
-               "pb_batch_free", "pb_set_butterfly_aggregation"]
+               "pb_batch_free", "pb_set_butterfly_aggregation", "pb_count_approx", "pb_graph_layout",
+               "pb_calibrate_atomics"]
 
 PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
 
@@ -125,6 +126,13 @@ def load_library(path: str = LIB_PATH):
         lib.pb_wedge_prefix.restype = i32
         lib.pb_sparsify.argtypes = [u32, u32, u64, vp, vp, i32, i32, ctypes.c_double, u64, vp, vp, u64p, vp]
         lib.pb_sparsify.restype = i32
+        lib.pb_count_approx.argtypes = [u32, u32, u64, vp, vp, i32, i32, ctypes.c_double, u64, i32, i32, u64,
+                                         ctypes.POINTER(ctypes.c_double), u64p, u64p, vp]
+        lib.pb_count_approx.restype = i32
+        lib.pb_calibrate_atomics.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+        lib.pb_calibrate_atomics.restype = i32
+        lib.pb_graph_layout.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
+        lib.pb_graph_layout.restype = i32
         lib.pb_autotune.argtypes = [vp, ctypes.POINTER(Plan)]
         lib.pb_batch_create.argtypes = [ctypes.POINTER(vp), u32, i32, u64, vp, ctypes.POINTER(vp)]
         lib.pb_batch_run.argtypes = [vp, vp]
@@ -160,6 +168,14 @@ def profile(enable: bool | None = None, reset: bool = False) -> dict:
     p = Profile()
     _check(lib.pb_profile_read(ctypes.byref(p)))
     return p.as_dict()
+
+
+def calibrate_atomics(scattered: bool = False, stream=None) -> float:
+    """64-bit L2 atomic-add throughput of the current device, operations/s
+    (pb_calibrate_atomics): coalesced (per-edge pattern) or scattered."""
+    out = ctypes.c_double()
+    _check(load_library().pb_calibrate_atomics(int(scattered), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def _torch():
@@ -206,8 +222,8 @@ SPARSIFY = {"edge": 0, "color": 1}
 
 
 def sparsify(nU: int, nV: int, u, v, kind: str, p: float, seed: int, stream=None):
-    """Kept edge pairs (host uint32 arrays) of edge or colourful
-    sparsification, and the scale 1/p^4 or 1/p^3 for the estimate."""
+    """Kept edge pairs (host uint32 arrays, input order) of edge or colourful
+    sparsification (pb_sparsify)."""
     lib = load_library()
     torch = _torch()
     pu, du, ku = _edge_arg(u, torch)
@@ -221,19 +237,32 @@ def sparsify(nU: int, nV: int, u, v, kind: str, p: float, seed: int, stream=None
     _check(lib.pb_sparsify(nU, nV, m, pu, pv, 0, SPARSIFY[kind], p, seed, ctypes.c_void_p(ou.ctypes.data),
                            ctypes.c_void_p(ov.ctypes.data), ctypes.byref(om), _stream(stream)))
     k = int(om.value)
-    scale = 1.0 / p ** 4 if kind == "edge" else 1.0 / p ** 3
-    return ou[:k].copy(), ov[:k].copy(), scale
+    return ou[:k].copy(), ov[:k].copy()
+
+
+@dataclass
+class Approx:
+    estimate: float
+    kept_count: int
+    kept_edges: int
 
 
 def approx_global(nU: int, nV: int, u, v, kind: str = "edge", p: float = 0.5, seed: int = 1,
-                  agg: str = "auto") -> float:
-    """Approximate total butterfly count: exact count of the sparsified graph,
-    scaled (Sec. "Approximate counting")."""
-    su, sv, scale = sparsify(nU, nV, u, v, kind, p, seed)
-    G = Graph.from_edges(nU, nV, su, sv).rank("degree")
-    c = G.count_global(agg)
-    G.free()
-    return c * scale
+                  agg: str = "auto", rank: str = "degree", scratch_bytes: int = 0, stream=None) -> Approx:
+    """pb_count_approx: approximate total butterfly count (Sec. "Approximate
+    counting"); sparsification, exact count of the kept graph and scaling all
+    run in the library."""
+    lib = load_library()
+    torch = _torch()
+    pu, du, ku = _edge_arg(u, torch)
+    pv, dv, kv = _edge_arg(v, torch)
+    if du != dv:
+        raise ValueError("u and v must both be on the device or both on the host")
+    est, kc, ke = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib.pb_count_approx(nU, nV, int(ku.shape[0]), pu, pv, du, SPARSIFY[kind], p, seed, RANKS[rank],
+                               AGGS[agg], scratch_bytes, ctypes.byref(est), ctypes.byref(kc), ctypes.byref(ke),
+                               _stream(stream)))
+    return Approx(est.value, int(kc.value), int(ke.value))
 
 
 @dataclass
@@ -316,6 +345,18 @@ class Graph:
         return dict(rank=inv_rank.get(p.rank_kind), retrieval=inv_rt.get(p.retrieval), hub_cluster=p.hub_cluster,
                     hub_min=p.hub_min, f_side=p.f_side, W_side=p.W_side, W_rank=p.W_rank,
                     max_owner_wedges=p.max_owner_wedges)
+
+    def layout(self, stream=None) -> dict:
+        """The PREPROCESS output as int32 CUDA tensors (uint32 bit patterns):
+        off, adj, cpos, degp (the input of count_noalloc) and label_of."""
+        torch = _torch()
+        n, na = self.nU + self.nV, 2 * self.info().m
+        t = {k: torch.empty(c, dtype=torch.int32, device="cuda") for k, c in
+             (("off", n + 1), ("adj", max(na, 1)), ("cpos", max(na, 1)), ("degp", n), ("label_of", n))}
+        p = lambda k: ctypes.c_void_p(t[k].data_ptr())  # noqa: E731
+        _check(load_library().pb_graph_layout(self._h, p("off"), p("adj"), p("cpos"), p("degp"), p("label_of"), 1,
+                                              _stream(stream)))
+        return t
 
     def ranks(self, stream=None) -> np.ndarray:
         out = np.empty(self.nU + self.nV, np.uint32)

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libpb.so")
-SOURCES = ["pb_prim.cu", "pb_graph.cu", "pb_count.cu", "pb_api.cu", "pb_noalloc.cu", "pb_sparsify.cu"]
+SOURCES = ["pb_prim.cu", "pb_graph.cu", "pb_count.cu", "pb_api.cu", "pb_noalloc.cu", "pb_sparsify.cu",
+           "pb_calibrate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

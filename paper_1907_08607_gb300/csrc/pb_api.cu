@@ -425,6 +425,24 @@ pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info) {
   return PB_OK;
 }
 
+pb_status pb_graph_layout(const pb_graph *g, uint32_t *off, uint32_t *adj, uint32_t *cpos, uint32_t *degp,
+                          uint32_t *label_of, int out_on_device, void *stream) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PB_TRY(ensure_ranked(g, s));
+  const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t na = 2 * g->m;
+  if (off) PB_CUDA(cudaMemcpyAsync(off, g->off, (g->n + 1) * sizeof(uint32_t), k, s));
+  if (adj && na) PB_CUDA(cudaMemcpyAsync(adj, g->adj, na * sizeof(uint32_t), k, s));
+  if (cpos && na) PB_CUDA(cudaMemcpyAsync(cpos, g->cpos, na * sizeof(uint32_t), k, s));
+  if (degp) PB_CUDA(cudaMemcpyAsync(degp, g->degp, g->n * sizeof(uint32_t), k, s));
+  if (label_of) PB_CUDA(cudaMemcpyAsync(label_of, g->label, g->n * sizeof(uint32_t), k, s));
+  PB_CUDA(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
 pb_status pb_graph_free(pb_graph *g) {
   clear_error();
   free_graph(g);

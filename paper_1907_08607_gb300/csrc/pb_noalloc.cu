@@ -32,8 +32,44 @@ void *g_na_addr[64];
 
 struct NaCtrl {                 // at the start of the scratch
   unsigned long long queue;     // next first endpoint to take
-  unsigned long long overflow;  // global sum wrapped past 2^64
+  unsigned long long overflow;  // a sum wrapped past 2^64
+  unsigned long long bad;       // the input layout failed validation
 };
+
+// Checks the caller's layout before any of it is used as an index: offsets
+// start at 0 and never decrease; every neighbour label is below n and on the
+// other side; every deg_x(y) entry is at most y's degree; every deg_x(x) at
+// most x's degree.  One warp per label.  On a violation the flag is set and the
+// counting kernel does nothing, so a malformed layout yields an error status
+// rather than an out-of-range access (off[n] must still be the length of adj
+// and cpos, which the library cannot see).
+__global__ void k_na_validate(uint64_t n, uint32_t nU, const uint32_t *__restrict__ off,
+                              const uint32_t *__restrict__ adj, const uint32_t *__restrict__ cpos,
+                              const uint32_t *__restrict__ degp, unsigned long long *bad) {
+  const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const uint32_t lane = lane_id();
+  for (uint64_t x = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    const uint32_t o0 = off[x], o1 = off[x + 1];
+    bool ok = o1 >= o0 && (x > 0 || o0 == 0) && degp[x] <= o1 - o0;
+    const bool xu = x < nU;
+    if (ok) {
+      for (uint32_t sl = o0 + lane; sl < o1; sl += 32) {
+        const uint32_t y = adj[sl];
+        if (y >= n || (y < nU) == xu) { ok = false; break; }
+        const uint32_t dy0 = off[y], dy1 = off[y + 1];
+        if (dy1 < dy0 || cpos[sl] > dy1 - dy0) { ok = false; break; }
+      }
+    }
+    if (!__all_sync(FULL, ok) && lane == 0) atomicOr(bad, 1ull);
+  }
+}
+
+// a + b, flagging a wrap past 2^64
+__device__ __forceinline__ unsigned long long na_add(unsigned long long a, unsigned long long b, bool &wrap) {
+  const unsigned long long r = a + b;
+  if (r < a) wrap = true;
+  return r;
+}
 
 __device__ __forceinline__ uint32_t na_find(const uint32_t *s_incl, uint32_t wi) {
   uint32_t lo = 0, hi = NA_THREADS - 1;  // first index with s_incl > wi
@@ -64,12 +100,18 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc(uint64_t n, uint32_t nU,
   __shared__ uint32_t s_incl[NA_THREADS], s_ex[NA_THREADS], s_oy[NA_THREADS];
   __shared__ unsigned long long s_sum[NA_THREADS];
   __shared__ uint32_t s_w[33];
-  __shared__ unsigned long long s_w64[33];
-  __shared__ uint32_t s_item, s_nt;
+  __shared__ unsigned long long s_own;
+  __shared__ uint32_t s_item, s_nt, s_wrap;
   const uint32_t tid = threadIdx.x;
   unsigned long long gacc = 0;
+  bool wrap = false;  // this thread saw a sum wrap past 2^64
+  if (__ldcg(&ctrl->bad)) return;  // the layout failed validation
   if (PV) s_sum[tid] = 0;
-  if (tid == 0) s_nt = 0;
+  if (tid == 0) {
+    s_nt = 0;
+    s_own = 0;
+    s_wrap = 0;
+  }
   for (;;) {
     if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&ctrl->queue, 1ull));
     __syncthreads();
@@ -110,16 +152,24 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc(uint64_t n, uint32_t nU,
     }
     const uint32_t nt = s_nt;
     // ---- endpoints
+    // Every per-vertex count is at most the global count, so checking every
+    // partial sum of the global count for a wrap covers the per-vertex sums.
     unsigned long long own = 0;
     for (uint32_t t = tid; t < nt; t += NA_THREADS) {
       const uint32_t x2 = T[t];
       unsigned long long d = __ldcg(&A[x2 - base]), b = d * (d - 1) / 2;
-      own += b;
+      own = na_add(own, b, wrap);
       if (PV && b) atomicAdd(&out_pv[x2], b);
     }
-    own = block_sum(own, s_w64);
+    if (own) {
+      const unsigned long long before = atomicAdd(&s_own, own);
+      if (before + own < before) wrap = true;
+    }
+    __syncthreads();
     if (tid == 0) {
-      gacc += own;
+      own = s_own;
+      s_own = 0;
+      gacc = na_add(gacc, own, wrap);
       if (PV && own) atomicAdd(&out_pv[x1], own);
     }
     // ---- centres: d - 1 per wedge, summed per neighbour
@@ -152,9 +202,14 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc(uint64_t n, uint32_t nU,
     __syncthreads();
     if (tid == 0) s_nt = 0;
   }
-  if (tid == 0 && gacc) {
-    unsigned long long old = atomicAdd(out_global, gacc);
-    if (old + gacc < old) atomicAdd(&ctrl->overflow, 1ull);
+  if (wrap) atomicOr(&s_wrap, 1u);
+  __syncthreads();
+  if (tid == 0) {
+    if (gacc) {
+      const unsigned long long old = atomicAdd(out_global, gacc);
+      if (old + gacc < old) s_wrap = 1;
+    }
+    if (s_wrap) atomicAdd(&ctrl->overflow, 1ull);
   }
 }
 
@@ -192,11 +247,15 @@ extern "C" pb_status pb_count_noalloc(uint64_t n, uint32_t nU, const uint32_t *o
     return fail(PB_ERR_INVALID, "a side of %llu vertices exceeds the no-allocation scratch (%llu MiB: at most %llu "
                 "vertices per side)", (unsigned long long)side, (unsigned long long)(NA_SCRATCH_BYTES >> 20),
                 (unsigned long long)(room / (2 * sizeof(uint32_t))));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sdev = 0, per_sm = 0;
+  PB_CUDA(cudaGetDevice(&dev));
+  PB_CUDA(cudaStreamGetDevice(s, &sdev));
+  if (sdev != dev)
+    return fail(PB_ERR_INVALID, "the stream belongs to device %d but device %d is current; make the stream's "
+                "device current before the call", sdev, dev);
   uint32_t *scratch = nullptr;
   PB_TRY(na_scratch_address(&scratch));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int dev = 0, per_sm = 0;
-  PB_CUDA(cudaGetDevice(&dev));
   auto kern = out_pv ? k_noalloc<true> : k_noalloc<false>;
   PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NA_THREADS, 0));
   uint64_t nslots = static_cast<uint64_t>(sm_count(dev)) * (per_sm > 0 ? per_sm : 1);
@@ -207,15 +266,20 @@ extern "C" pb_status pb_count_noalloc(uint64_t n, uint32_t nU, const uint32_t *o
   PB_CUDA(cudaMemsetAsync(scratch, 0, NA_CTRL_BYTES + nslots * slot_bytes, s));
   PB_CUDA(cudaMemsetAsync(out_global, 0, sizeof(uint64_t), s));
   if (out_pv) PB_CUDA(cudaMemsetAsync(out_pv, 0, n * sizeof(uint64_t), s));
+  NaCtrl *ctrl = reinterpret_cast<NaCtrl *>(scratch);
+  k_na_validate<<<grid_for(n * 32, 256, 8192), 256, 0, s>>>(n, nU, off, adj, cpos, degp, &ctrl->bad);
+  count_launch();
   kern<<<static_cast<unsigned>(nslots), NA_THREADS, 0, s>>>(n, nU, off, adj, cpos, degp, scratch, side,
                                                             reinterpret_cast<unsigned long long *>(out_global),
                                                             reinterpret_cast<unsigned long long *>(out_pv));
   count_launch();
   PB_CUDA(cudaGetLastError());
-  unsigned long long ovf = 0;
-  PB_CUDA(cudaMemcpyAsync(&ovf, &reinterpret_cast<NaCtrl *>(scratch)->overflow, sizeof(ovf),
-                          cudaMemcpyDeviceToHost, s));
+  NaCtrl h = {};
+  PB_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
   PB_CUDA(cudaStreamSynchronize(s));
-  if (ovf) return fail(PB_ERR_OVERFLOW, "global butterfly count exceeds 2^64");
+  if (h.bad)
+    return fail(PB_ERR_INVALID, "malformed layout: offsets not starting at 0 or decreasing, a neighbour label out of "
+                "range or on the same side, or a deg_x(y) / deg_x(x) entry above the degree");
+  if (h.overflow) return fail(PB_ERR_OVERFLOW, "global butterfly count exceeds 2^64");
   return PB_OK;
 }
