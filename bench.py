@@ -182,22 +182,31 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def measured_traffic(kernel: str, wedges_per_launch: float):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture,
-    scaled by wedges; None when the capture is of another kernel or the
-    kernel source has changed since."""
+def measured_traffic(workload: str, phase: str, wedges_per_launch: float):
+    """DRAM bytes per launch of the tier kernel of `phase` from the committed
+    ncu capture of this workload (or of its reduced-scale copy), scaled by
+    wedges; None when no capture covers it or the kernel source has changed
+    since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        with open(os.path.join(ROOT, t["source_file"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
     except Exception:
         return None
-    k = t.get("kernels", {}).get(kernel)
-    if k is None or sha != t.get("source_sha256"):
-        return None
-    return k["dram_bytes_per_wedge"] * wedges_per_launch
+    for cap in t.get("captures", []):
+        if workload not in (cap.get("workload"), cap.get("scales_to")):
+            continue
+        k = cap.get("kernels", {}).get(phase)
+        if k is None:
+            continue
+        try:
+            with open(os.path.join(ROOT, cap["source_file"]), "rb") as f:
+                sha = hashlib.sha256(f.read()).hexdigest()
+        except OSError:
+            continue
+        if sha == cap.get("source_sha256"):
+            return k["dram_bytes_per_wedge"] * wedges_per_launch
+    return None
 
 
 def measured_peaks():
@@ -327,6 +336,12 @@ def run_gb300(args):
         step()
     torch.cuda.synchronize()
 
+    # the L2 atomic ceiling for the roofline (a few ms, before the timed region)
+    try:
+        atomics_peak = pb.calibrate_atomics(False)
+    except Exception:
+        atomics_peak = None
+
     # ---- timed region: device-resident inputs
     pb.profile(enable=True, reset=True)
     l0 = pb.kernel_launches()
@@ -393,7 +408,7 @@ def run_gb300(args):
                "ms_per_step": ems / args.steps}
 
     # ---- roofline of the dominant kernel (CUDA events inside the library)
-    kern = max(["light", "medium", "heavy", "sort"], key=lambda k: prof[k]["ms"])
+    kern = max(["light", "medium", "large", "heavy", "sort"], key=lambda k: prof[k]["ms"])
     kp = prof[kern]
     peak, peak_src = measured_peaks()
     roof = None
@@ -401,13 +416,25 @@ def run_gb300(args):
         per_launch_ms = kp["ms"] / kp["records"]
         per_launch_bytes = BYTES_PER_WEDGE[args.outputs] * kp["wedges"] / kp["records"]
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-        traffic = measured_traffic(kern, kp["wedges"] / kp["records"])
+        traffic = measured_traffic(args.workload, kern, kp["wedges"] / kp["records"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kern, "peak_source": peak_src,
                 "launch_ms": per_launch_ms, "algorithmic_bytes_per_launch": per_launch_bytes}
         if traffic:  # the DRAM bytes the kernel moves (ncu), over the same launch time
             roof["traffic_gbs"] = traffic / (per_launch_ms / 1e3) / 1e9
             roof["traffic_frac"] = roof["traffic_gbs"] / peak
+        # Second ceiling: the device's 64-bit L2 atomic-add throughput (measured
+        # by the library's calibration kernel in this process).  Per-edge counts
+        # take one counter update per wedge, per-vertex one per wedge (centre)
+        # in the streaming model; global counts need none per wedge.
+        if atomics_peak:
+            per_wedge = {"all": 2, "edge": 1, "vertex": 1, "global": 0}[args.outputs]
+            if per_wedge:
+                ops = per_wedge * kp["wedges"] / kp["records"] / (per_launch_ms / 1e3)
+                roof["l2_atomic"] = {"achieved_ops_per_s": ops, "peak_ops_per_s": atomics_peak,
+                                     "frac": ops / atomics_peak, "updates_per_wedge": per_wedge,
+                                     "peak_pattern": "coalesced 64-bit reductions, 32 consecutive counters per warp"}
+        roof["l2_atomic_frac"] = roof.get("l2_atomic", {}).get("frac")
 
     if rank != 0:
         if dist is not None:
@@ -508,6 +535,30 @@ def run_batched(args):
     batch_ms = e0.elapsed_time(e1) / args.steps
     glob = B.globals()
     same = all(int(glob[i]) == G.count_global("auto") for i, G in enumerate(Gs[:64]))
+    B.free()
+    # The autotuner's per-graph choices, and the same batch with every graph
+    # pinned to one fixed plan (no large tier, dense heavy slots: the plan
+    # before per-graph tuning), timed the same way.
+    plans = [G.autotune() for G in Gs]
+    chosen = {}
+    for p in plans:
+        key = f"agg={p['agg']},large_max={p['large_max']},hot={p['hot']}"
+        chosen[key] = chosen.get(key, 0) + 1
+    for G, p in zip(Gs, plans):
+        G.set_plan(dict(p, agg="batch", light_max=768, med_max=4096, large_max=4096, hot=16384))
+    Bf = pb.Batch(Gs, vertex=True)
+    for _ in range(max(3, args.warmup)):
+        Bf.run()
+    e0.record(stream)
+    for _ in range(args.steps):
+        Bf.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fixed_ms = e0.elapsed_time(e1) / args.steps
+    same = same and all(int(a) == int(b) for a, b in zip(Bf.globals(), glob))
+    Bf.free()
+    for G in Gs:
+        G.set_plan(None)
     line = {"metric": METRIC, "mode": "batched", "value": W / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": batch_ms, "higher_is_better": True,
             "dtype": "u64", "data": "synthetic",
@@ -518,9 +569,12 @@ def run_batched(args):
                       "per_graph_latency_ms": {"p50": 1e3 * _pct(lat, 50), "p99": 1e3 * _pct(lat, 99)}},
             "batched_latency_ms": {"p50": 1e3 * _pct(blat, 50), "p99": 1e3 * _pct(blat, 99)},
             "speedup_vs_plain": plain_ms / batch_ms, "gpu_launches": launches,
+            "autotuned_plans": chosen,
+            "fixed_plan": {"value": W / (fixed_ms / 1e3), "ms_per_step": fixed_ms,
+                           "plan": "light_max 768, med_max 4096, no large tier, dense heavy slots, hot 16384"},
+            "speedup_vs_fixed_plan": fixed_ms / batch_ms,
             "results_equal_alone_and_in_batch": same}
     print(json.dumps(line), flush=True)
-    B.free()
     for G in Gs:
         G.free()
     return 0

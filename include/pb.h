@@ -256,27 +256,73 @@ pb_status pb_count_approx(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *
                           pb_agg agg, uint64_t scratch_bytes, double *estimate, uint64_t *kept_count,
                           uint64_t *kept_edges, void *stream);
 
-/* Autotuner: a plan from the graph's degree and wedge statistics.
- *  f_side = (W_side - W_rank) / W_side, W_side the wedges of side order (the
- *  fewer of sum C(deg v, 2) over V and over U), W_rank those of the current
- *  ranking: the paper's ranking-choice metric (Sec. "Experiments", Table 3);
- *  side order is recommended when f_side < 0.1.
+/* Autotuner: a counting plan from the graph's degree and wedge statistics,
+ * for a scratch budget (scratch_bytes as for pb_count_global, 0 = 16 GiB).
+ *  rank_kind: f_side = (W_side - W_rank) / W_side, W_side the wedges of side
+ *    order (the fewer of sum C(deg v, 2) over V and over U), W_rank those of
+ *    the current ranking: the paper's ranking-choice metric (Sec.
+ *    "Experiments", Table 3); side order is recommended when f_side < 0.1.
  *  retrieval: the endpoint that gives the smaller largest per-owner wedge
- *  count (load balance; the higher-ranked one almost always).
- *  hub_min / hub_cluster: owners above hub_min wedges are given a cluster of
- *  hub_cluster blocks (hub_min = UINT64_MAX when no owner needs one).
- * pb_count_* with PB_AGG_AUTO and PB_RETRIEVE_AUTO follow this plan. */
+ *    count (load balance; the higher-ranked one almost always).
+ *  Work tiers, from the per-owner wedge counts under that retrieval: owners
+ *    with at most light_max wedges (<= 768) are counted one warp each in a
+ *    shared-memory hash table; those up to med_max (<= 4096) one 512-thread
+ *    block each in a shared-memory hash table; those up to large_max
+ *    (<= 65535; the autotuner sets large_max = med_max, which leaves this
+ *    tier empty, as the heavy kernel's split work units count such owners at
+ *    least as fast) one 256-thread block each, with 16-bit counts of the
+ *    first 16384 labels of a side in shared memory and the rest in a small
+ *    hash table in device memory; the rest ("heavy") one 1024-thread block each
+ *    with the counts of the first `hot` labels of a side in shared memory and
+ *    the rest in device-memory scratch.  hot is the size whose share of
+ *    wedge endpoints (hot_hit) pays for its shared memory: 16384 labels, or
+ *    49152 when the smaller range catches under 90 % of the endpoints.
+ *  agg (used by PB_AGG_AUTO), from the heavy owners' scratch per slot against
+ *    the budget and the device's resident blocks:
+ *    BATCH when one dense histogram per resident block fits the budget;
+ *    HASH (the dense histogram's cold part replaced by a hash table sized by
+ *    the owner's distinct bound) when only those smaller slots fit;
+ *    HIST when a single owner holds more than eight times a block's share of
+ *    the heavy wedges: owners above hub_min wedges then take a cluster of
+ *    hub_cluster blocks (hub_min = UINT64_MAX when no owner needs one).
+ *    SORT is never chosen (on the GPU it trails the others several-fold).
+ *    With fit_d and fit_h the dense and hashed slots the budget holds and
+ *    want = min(resident_blocks, heavy owners): BATCH if fit_d >= want or
+ *    fit_d >= fit_h, else HASH.
+ *  heavy_slots / slot_bytes: concurrently processed heavy owners and the
+ *    device memory each takes under that choice.
+ * pb_count_* with PB_AGG_AUTO follow this plan (computed per call unless one
+ * is pinned with pb_set_plan); explicit aggregations keep their own heavy
+ * path and take light_max, med_max and hot from it. */
 typedef struct {
   int32_t rank_kind;    /* recommended pb_rank_kind */
   int32_t retrieval;    /* pb_retrieval (LOW or HIGH) */
-  int32_t agg;          /* pb_agg */
+  int32_t agg;          /* pb_agg for PB_AGG_AUTO: BATCH, HASH or HIST */
   uint32_t hub_cluster;
   uint64_t hub_min;
   double f_side;
   uint64_t W_side, W_rank;
   uint64_t max_owner_wedges;  /* under the chosen retrieval */
+  uint32_t light_max, med_max, large_max, hot, heavy_slots;
+  double hot_hit;             /* share of wedges whose second endpoint is hot */
+  uint64_t owners[4];         /* light, medium, large, heavy owners */
+  uint64_t wedges[4];         /* their wedges */
+  uint64_t slot_bytes;        /* device memory per heavy slot under agg */
+  uint64_t slot_bytes_dense;  /* ... with a dense histogram (BATCH, HIST) */
+  uint64_t slot_bytes_hash;   /* ... with a hashed cold part (HASH) */
+  uint32_t resident_blocks;   /* resident blocks of the heavy kernel */
+  double mid_segment;         /* wedges per neighbour of the owners between med_max and 65535 wedges */
+  uint64_t scratch_bytes;     /* the budget the plan was made for */
 } pb_plan_t;
-pb_status pb_autotune(const pb_graph *g, pb_plan_t *plan);
+pb_status pb_autotune(const pb_graph *g, uint64_t scratch_bytes, pb_plan_t *plan);
+
+/* Pins a plan for later PB_AGG_AUTO counts on g (NULL returns to planning
+ * per call).  light_max is clamped to [1, 768], med_max to [light_max, 4096],
+ * large_max to [med_max, 65535],
+ * hot to [0, 49152]; PB_ERR_INVALID for an agg other than BATCH, HASH or
+ * HIST, a retrieval other than LOW or HIGH, or hub_cluster outside [1, 16].
+ * Counts are exact under every plan. */
+pb_status pb_set_plan(pb_graph *g, const pb_plan_t *plan);
 
 /* Batched counting: many ranked graphs counted by one persistent kernel per
  * work tier over all their owners, the launches captured once in a CUDA
@@ -306,6 +352,27 @@ pb_status pb_batch_free(pb_batch *b);
  * no ranking. */
 pb_status pb_graph_layout(const pb_graph *g, uint32_t *off, uint32_t *adj, uint32_t *cpos, uint32_t *degp,
                           uint32_t *label_of, int out_on_device, void *stream);
+
+/* Upper bound on the device memory a count on g with these arguments will
+ * allocate (outputs, tier lists, heavy-tier scratch, download staging), for
+ * admission control: the library's stream-ordered pool rounds each allocation
+ * up, which the bound includes.  Runs the planner's statistics pass on the
+ * legacy default stream, into memory of its own; like pb_autotune it only
+ * reads a ranked graph, so it may run while that graph is counted. */
+pb_status pb_count_bytes(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, int want_vertex, int want_edge,
+                         int out_on_device, uint64_t *bytes);
+
+/* The persistent tier kernels of later counts on g take this share, in
+ * (0, 1], of the device's resident blocks (default 1).  Counts running at the
+ * same time on other streams then share the SMs instead of waiting for a
+ * kernel that holds all of them.  Results do not depend on it. */
+pb_status pb_set_grid_share(pb_graph *g, double share);
+
+/* Memory of the current device's default stream-ordered pool, which every
+ * library allocation comes from: bytes in use now and the high-water mark
+ * since the last reset (reset_peak != 0 resets it to the current use first).
+ * Measurement support for checking pb_count_bytes. */
+pb_status pb_device_memory(int reset_peak, uint64_t *used, uint64_t *peak);
 
 /* Releases the graph and every device buffer it holds.  NULL is accepted. */
 pb_status pb_graph_free(pb_graph *g);
@@ -373,10 +440,11 @@ enum {
   PB_PHASE_CLASSIFY = 2, /* binning first endpoints by wedge count */
   PB_PHASE_LIGHT = 3,    /* warp-per-endpoint shared-memory hash kernel */
   PB_PHASE_MEDIUM = 4,   /* block-per-endpoint shared-memory hash kernel */
-  PB_PHASE_HEAVY = 5,    /* cluster-per-endpoint device-memory kernel */
+  PB_PHASE_HEAVY = 5,    /* block-per-endpoint hot-range kernel, 1024 threads (or clusters) */
   PB_PHASE_SORT = 6,     /* sort aggregation (all its kernels) */
   PB_PHASE_OUTPUT = 7,   /* rank space -> id space / input order, downloads */
-  PB_NPHASE = 8
+  PB_PHASE_LARGE = 8,    /* block-per-endpoint hot-range kernel, 256 threads */
+  PB_NPHASE = 9
 };
 typedef struct {
   double ms[PB_NPHASE];         /* accumulated device time */

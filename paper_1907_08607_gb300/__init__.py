@@ -40,9 +40,10 @@ ABI_SYMBOLS = ["pb_graph_from_edges", "pb_rank", "pb_rank_custom", "pb_graph_ran
                "pb_set_retrieval", "pb_count_owner_range", "pb_wedge_prefix", "pb_sparsify", "pb_autotune",
                "pb_batch_create", "pb_batch_run", "pb_batch_globals", "pb_batch_vertex", "pb_batch_wedges",
                "pb_batch_free", "pb_set_butterfly_aggregation", "pb_count_approx", "pb_graph_layout",
-               "pb_calibrate_atomics"]
+               "pb_calibrate_atomics", "pb_set_plan", "pb_count_bytes", "pb_set_grid_share",
+               "pb_device_memory"]
 
-PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output"]
+PHASES = ["build", "rank", "classify", "light", "medium", "heavy", "sort", "output", "large"]
 
 _lock = threading.Lock()
 _lib = None
@@ -64,12 +65,17 @@ class GraphInfo(ctypes.Structure):
 class Plan(ctypes.Structure):
     _fields_ = [("rank_kind", ctypes.c_int32), ("retrieval", ctypes.c_int32), ("agg", ctypes.c_int32),
                 ("hub_cluster", ctypes.c_uint32), ("hub_min", ctypes.c_uint64), ("f_side", ctypes.c_double),
-                ("W_side", ctypes.c_uint64), ("W_rank", ctypes.c_uint64), ("max_owner_wedges", ctypes.c_uint64)]
+                ("W_side", ctypes.c_uint64), ("W_rank", ctypes.c_uint64), ("max_owner_wedges", ctypes.c_uint64),
+                ("light_max", ctypes.c_uint32), ("med_max", ctypes.c_uint32), ("large_max", ctypes.c_uint32),
+                ("hot", ctypes.c_uint32), ("heavy_slots", ctypes.c_uint32), ("hot_hit", ctypes.c_double),
+                ("owners", ctypes.c_uint64 * 4), ("wedges", ctypes.c_uint64 * 4), ("slot_bytes", ctypes.c_uint64), ("slot_bytes_dense", ctypes.c_uint64),
+                ("slot_bytes_hash", ctypes.c_uint64), ("resident_blocks", ctypes.c_uint32),
+                ("mid_segment", ctypes.c_double), ("scratch_bytes", ctypes.c_uint64)]
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8),
-                ("wedges", ctypes.c_uint64 * 8), ("records", ctypes.c_uint64 * 8)]
+    _fields_ = [("ms", ctypes.c_double * 9), ("launches", ctypes.c_uint64 * 9),
+                ("wedges", ctypes.c_uint64 * 9), ("records", ctypes.c_uint64 * 9)]
 
     def as_dict(self):
         return {ph: dict(ms=self.ms[i], launches=int(self.launches[i]), wedges=int(self.wedges[i]),
@@ -133,7 +139,15 @@ def load_library(path: str = LIB_PATH):
         lib.pb_calibrate_atomics.restype = i32
         lib.pb_graph_layout.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
         lib.pb_graph_layout.restype = i32
-        lib.pb_autotune.argtypes = [vp, ctypes.POINTER(Plan)]
+        lib.pb_autotune.argtypes = [vp, u64, ctypes.POINTER(Plan)]
+        lib.pb_count_bytes.argtypes = [vp, i32, u64, i32, i32, i32, u64p]
+        lib.pb_count_bytes.restype = i32
+        lib.pb_set_grid_share.argtypes = [vp, ctypes.c_double]
+        lib.pb_set_grid_share.restype = i32
+        lib.pb_device_memory.argtypes = [i32, u64p, u64p]
+        lib.pb_device_memory.restype = i32
+        lib.pb_set_plan.argtypes = [vp, ctypes.POINTER(Plan)]
+        lib.pb_set_plan.restype = i32
         lib.pb_batch_create.argtypes = [ctypes.POINTER(vp), u32, i32, u64, vp, ctypes.POINTER(vp)]
         lib.pb_batch_run.argtypes = [vp, vp]
         lib.pb_batch_globals.argtypes = [vp, u64p, vp]
@@ -176,6 +190,13 @@ def calibrate_atomics(scattered: bool = False, stream=None) -> float:
     out = ctypes.c_double()
     _check(load_library().pb_calibrate_atomics(int(scattered), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+def device_memory(reset_peak: bool = False) -> tuple[int, int]:
+    """(bytes in use, high-water mark) of the library's device memory pool."""
+    used, peak = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().pb_device_memory(int(reset_peak), ctypes.byref(used), ctypes.byref(peak)))
+    return int(used.value), int(peak.value)
 
 
 def _torch():
@@ -336,15 +357,53 @@ class Graph:
         _check(load_library().pb_set_butterfly_aggregation(self._h, BUTTERFLY_AGGS[which]))
         return self
 
-    def autotune(self) -> dict:
-        """The autotuner's plan for this graph (see pb_autotune)."""
+    def autotune(self, scratch_bytes: int = 0) -> dict:
+        """The autotuner's plan for this graph and scratch budget (pb_autotune)."""
         p = Plan()
-        _check(load_library().pb_autotune(self._h, ctypes.byref(p)))
+        _check(load_library().pb_autotune(self._h, scratch_bytes, ctypes.byref(p)))
         inv_rank = {v: k for k, v in RANKS.items()}
         inv_rt = {v: k for k, v in RETRIEVALS.items()}
-        return dict(rank=inv_rank.get(p.rank_kind), retrieval=inv_rt.get(p.retrieval), hub_cluster=p.hub_cluster,
-                    hub_min=p.hub_min, f_side=p.f_side, W_side=p.W_side, W_rank=p.W_rank,
-                    max_owner_wedges=p.max_owner_wedges)
+        inv_agg = {v: k for k, v in AGGS.items()}
+        return dict(rank=inv_rank.get(p.rank_kind), retrieval=inv_rt.get(p.retrieval), agg=inv_agg.get(p.agg),
+                    hub_cluster=p.hub_cluster, hub_min=p.hub_min, f_side=p.f_side, W_side=p.W_side, W_rank=p.W_rank,
+                    max_owner_wedges=p.max_owner_wedges, light_max=p.light_max, med_max=p.med_max,
+                    large_max=p.large_max, hot=p.hot,
+                    heavy_slots=p.heavy_slots, hot_hit=p.hot_hit, owners=list(p.owners), wedges=list(p.wedges),
+                    slot_bytes=p.slot_bytes, slot_bytes_dense=p.slot_bytes_dense, slot_bytes_hash=p.slot_bytes_hash,
+                    resident_blocks=p.resident_blocks, mid_segment=p.mid_segment, scratch_bytes=p.scratch_bytes)
+
+    def count_bytes(self, agg: str = "auto", scratch_bytes: int = 0, vertex: bool = True, edge: bool = True,
+                    on_device: bool = False) -> int:
+        """Upper bound on the device memory such a count allocates (pb_count_bytes)."""
+        out = ctypes.c_uint64()
+        _check(load_library().pb_count_bytes(self._h, AGGS[agg], scratch_bytes, int(vertex), int(edge),
+                                             int(on_device), ctypes.byref(out)))
+        return int(out.value)
+
+    def set_grid_share(self, share: float) -> "Graph":
+        """Share of the device's resident blocks later counts take (pb_set_grid_share)."""
+        _check(load_library().pb_set_grid_share(self._h, share))
+        return self
+
+    def set_plan(self, plan: dict | None) -> "Graph":
+        """Pins a plan (a dict as autotune() returns, fields may be changed)
+        for later "auto" counts; None returns to planning per count."""
+        lib = load_library()
+        if plan is None:
+            _check(lib.pb_set_plan(self._h, None))
+            return self
+        p = Plan()
+        p.rank_kind = RANKS.get(plan.get("rank") or "degree", 1)
+        p.retrieval = RETRIEVALS[plan["retrieval"]]
+        p.agg = AGGS[plan["agg"]]
+        p.hub_cluster = plan.get("hub_cluster", 1)
+        p.hub_min = plan.get("hub_min", 2 ** 64 - 1)
+        p.light_max = plan.get("light_max", 768)
+        p.med_max = plan.get("med_max", 4096)
+        p.large_max = plan.get("large_max", 4096)
+        p.hot = plan.get("hot", 16384)
+        _check(lib.pb_set_plan(self._h, ctypes.byref(p)))
+        return self
 
     def layout(self, stream=None) -> dict:
         """The PREPROCESS output as int32 CUDA tensors (uint32 bit patterns):

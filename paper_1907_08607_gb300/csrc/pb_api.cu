@@ -135,6 +135,16 @@ pb_status ensure_scratch(pb_graph *g, size_t bytes, cudaStream_t s) {
   return PB_OK;
 }
 
+pb_status ensure_scratch2(pb_graph *g, size_t bytes, cudaStream_t s) {
+  if (g->scratch2_cap >= bytes) return PB_OK;
+  dfree(g->scratch2, s);
+  g->scratch2 = nullptr;
+  g->scratch2_cap = 0;
+  PB_TRY(dalloc(&g->scratch2, bytes, s));
+  g->scratch2_cap = bytes;
+  return PB_OK;
+}
+
 int sm_count(int device) {
   static int cached[64] = {0};
   if (device >= 0 && device < 64 && cached[device]) return cached[device];
@@ -155,7 +165,7 @@ static void free_graph(pb_graph *g) {
   cudaStream_t s = 0;
   free_ranked(g, s);
   dfree(g->in2c, s); dfree(g->eu, s); dfree(g->ev, s); dfree(g->deg, s);
-  dfree(g->scratch, s); dfree(g->pv, s); dfree(g->es, s); dfree(g->acc, s);
+  dfree(g->scratch, s); dfree(g->scratch2, s); dfree(g->pv, s); dfree(g->es, s); dfree(g->es32, s); dfree(g->acc, s); dfree(g->tstat, s);
   cudaStreamSynchronize(s);
   cudaGetLastError();
   cudaSetDevice(cur);
@@ -420,7 +430,8 @@ pb_status pb_graph_info(const pb_graph *g, pb_graph_info_t *info) {
   if (g->rank_kind >= 0) b += 4 * (g->n + 1) * 4 + (g->n + 1) * 8 + 2 * (2 * g->m + 1) * 4 + 2 * (g->m + 1) * 4;
   if (g->pv) b += (g->n + 1) * 8;
   if (g->es) b += (2 * g->m + 1) * 8;
-  b += g->scratch_cap;
+  if (g->es32) b += (2 * g->m + 1) * 4;
+  b += g->scratch_cap + g->scratch2_cap;
   info->device_bytes = b;
   return PB_OK;
 }
@@ -440,6 +451,32 @@ pb_status pb_graph_layout(const pb_graph *g, uint32_t *off, uint32_t *adj, uint3
   if (degp) PB_CUDA(cudaMemcpyAsync(degp, g->degp, g->n * sizeof(uint32_t), k, s));
   if (label_of) PB_CUDA(cudaMemcpyAsync(label_of, g->label, g->n * sizeof(uint32_t), k, s));
   PB_CUDA(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
+pb_status pb_set_grid_share(pb_graph *g, double share) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  if (!(share > 0.0 && share <= 1.0)) return fail(PB_ERR_INVALID, "share must be in (0, 1]");
+  g->grid_share = share;
+  return PB_OK;
+}
+
+pb_status pb_device_memory(int reset_peak, uint64_t *used, uint64_t *peak) {
+  clear_error();
+  int dev = 0;
+  PB_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  PB_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  unsigned long long u = 0, h = 0;  // the pool attributes are 64-bit
+  PB_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+  if (reset_peak) {
+    unsigned long long zero = 0;
+    PB_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+  }
+  PB_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &h));
+  if (used) *used = u;
+  if (peak) *peak = h;
   return PB_OK;
 }
 

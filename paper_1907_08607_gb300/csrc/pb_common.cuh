@@ -54,10 +54,19 @@ struct pb_graph {
   // Aggregation scratch, grown on demand and kept until pb_graph_free.
   void *scratch = nullptr;
   size_t scratch_cap = 0;
+  void *scratch2 = nullptr;  // the medium tier's slots
+  size_t scratch2_cap = 0;
   // Count outputs in rank space (kept to avoid reallocating per call).
   uint64_t *pv = nullptr;     // [n]
   uint64_t *es = nullptr;     // [2m] per-slot edge partial counts
+  uint32_t *es32 = nullptr;   // [2m] per-slot 32-bit partials (carries go to es)
   unsigned long long *acc = nullptr;  // [8] global sum, overflow word, work queues
+  unsigned long long *tstat = nullptr;  // autotuner statistics of the owners
+  // A plan pinned by pb_set_plan (used by PB_AGG_AUTO counts instead of one
+  // computed per call).
+  bool has_plan = false;
+  pb_plan_t plan = {};
+  double grid_share = 1.0;  // share of resident blocks the tier kernels take (pb_set_grid_share)
 };
 
 namespace pb {
@@ -114,6 +123,7 @@ inline pb_status dalloc_t(T **p, size_t count, cudaStream_t s) {
   return dalloc(reinterpret_cast<void **>(p), count * sizeof(T), s);
 }
 pb_status ensure_scratch(pb_graph *g, size_t bytes, cudaStream_t s);
+pb_status ensure_scratch2(pb_graph *g, size_t bytes, cudaStream_t s);
 int sm_count(int device);
 
 // ---- primitives (pb_prim.cu) ---------------------------------------------
@@ -156,7 +166,8 @@ struct CountOut {
 };
 pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut &o,
                     cudaStream_t s);
-void make_plan(const pb_graph *g, pb_plan_t *plan);
+void make_plan_basic(const pb_graph *g, pb_plan_t *plan);
+pb_status make_plan(pb_graph *g, uint64_t budget, cudaStream_t s, pb_plan_t *plan);
 
 // head[i] = 1 where keys[i] starts a run of equal keys (pb_graph.cu).
 __global__ void k_heads(const uint64_t *__restrict__ keys, size_t m, uint32_t *__restrict__ head);

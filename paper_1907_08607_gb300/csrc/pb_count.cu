@@ -26,6 +26,7 @@
 // flattened with a prefix sum over deg_x1(y) and spread evenly over threads.
 #include <cooperative_groups.h>
 
+#include <cmath>
 #include <cstdlib>
 #include <new>
 #include <string>
@@ -48,12 +49,15 @@ struct CArgs {
   int rev;                  // 1: wedges are owned by their higher-ranked endpoint
   unsigned long long *pv;   // [n] by label, or null
   unsigned long long *es;   // [2m] per slot, or null
+  unsigned int *es32;       // [2m] per-slot 32-bit partials of the per-wedge contributions, or null
+  uint32_t nlim[2];         // y's list takes 32-bit partials when deg(y) - 1 <= nlim[side of its entries]
   unsigned long long *acc;  // [0] global, [1] overflow, [2..] work queues
 };
 
+// Accumulator words: the global count and its overflow word, the work queues
+// of the block tiers, the list cursors of the tier split, an error word.
 enum { ACC_GLOBAL = 0, ACC_OVF = 1, ACC_QMED = 2, ACC_QHEAVY = 3, ACC_NLIGHT = 4, ACC_NMED = 5,
-       ACC_NHEAVY = 6, ACC_ERR = 7, ACC_WLIGHT = 8, ACC_WMED = 9, ACC_WHEAVY = 10, ACC_NHUB = 11,
-       ACC_WORDS = 16 };
+       ACC_NLARGE = 6, ACC_NHEAVY = 7, ACC_ERR = 8, ACC_NHUB = 9, ACC_QLARGE = 10, ACC_WORDS = 16 };
 
 // Probe loops are bounded by the table size; running past it (impossible at
 // load <= 1/2 unless scratch is corrupt) records an error instead of spinning.
@@ -70,6 +74,24 @@ constexpr int MB_CAP = 8192;          // per-block table entries (>= 2 * MED_MAX
 // medium-tier dynamic shared memory: keys, 16-bit counts, 16-bit table position per wedge
 constexpr size_t MB_SMEM = (MB_CAP + MB_CAP / 2) * sizeof(uint32_t) + MED_MAX * sizeof(uint16_t);
 constexpr int HB_THREADS = 1024;
+
+// Per-wedge edge contributions of the heavy tiers go to 32-bit per-slot
+// partial counters where they cannot wrap: the count of edge (x2, y) is at
+// most (deg(x2) - 1)(deg(y) - 1) (a butterfly through the edge picks one other
+// neighbour of each endpoint), so every slot of y's list is safe when
+// deg(y) - 1 <= nlim, nlim = (2^32 - 1) / (largest degree on x2's side - 1).
+// On an array far larger than L2, where most reductions miss, a 4-byte
+// reduction moves half the sector bytes of an 8-byte one.  The lists of the
+// few centres above the limit keep 64-bit counters.  An edge's count is the
+// sum of both arrays over its two slots.
+__device__ __forceinline__ bool es_narrow(const CArgs &a, uint32_t x1, uint32_t dy) {
+  return dy - 1 <= a.nlim[x1 < a.nU ? 0 : 1];
+}
+
+__device__ __forceinline__ void es_add_wedge(const CArgs &a, uint32_t sl, uint32_t t, bool narrow) {
+  if (narrow) atomicAdd(&a.es32[sl], t);
+  else atomicAdd(&a.es[sl], static_cast<unsigned long long>(t));
+}
 
 __device__ __forceinline__ void add_global(unsigned long long *acc, unsigned long long v) {
   if (!v) return;
@@ -784,6 +806,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
   const uint32_t slot = blockIdx.x / csize;
   const uint32_t tid = threadIdx.x;
   __shared__ uint32_t s_incl[HB_THREADS], s_ex[HB_THREADS], s_oy[HB_THREADS];
+  __shared__ uint8_t s_nar[HB_THREADS];  // the neighbour's list takes 32-bit edge partials
   __shared__ unsigned long long s_sum[HB_THREADS];
   __shared__ uint32_t s_w[33];
   __shared__ unsigned long long s_w64[33];
@@ -896,6 +919,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
         const bool v = i < dp;
         uint32_t y, c, oy;
         owner_nbr(a, xbase, i, v, y, c, oy);
+        if (PE) s_nar[tid] = v && es_narrow(a, x1, a.off[y + 1] - a.off[y]);
         uint32_t tot;
         const uint32_t incl = block_incl_scan(c, s_w, &tot);
         s_incl[tid] = incl;
@@ -924,7 +948,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
 #pragma unroll
           for (int q = 0; q < HB_BATCH; q++) {
             unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
-            if (PE && t) atomicAdd(&a.es[slv[q]], t);
+            if (PE && t) es_add_wedge(a, slv[q], static_cast<uint32_t>(t), s_nar[srcv[q]]);
             warp_run_add(s_sum, srcv[q], t);
           }
         }
@@ -961,33 +985,160 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy(CArgs a0, const uint32_t *
 }
 
 // ---------------------------------------------------------------------------
-// Heavy tier, one block per owner with a dense slot (no cluster): the owner's
+// Heavy tier, one block per owner and slot (no cluster): the owner's
 // neighbours are staged HB_THREADS at a time, and each warp takes whole
 // neighbours from a shared counter and walks the neighbour's segment of
 // second endpoints with its lanes (coalesced adjacency reads).  Counts of the
-// first h.hot labels of the side live in shared memory, the rest in the
-// slot's device-memory histogram; a touched list (device memory, counter in
-// shared memory) records each distinct second endpoint once.  The second
-// pass sums d - 1 over a segment in registers and adds it to the centre once.
-template <bool PV, bool PE, bool MULTI>
-__global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
-                                                       HeavySlots h, const uint64_t *__restrict__ items,
-                                                       const CArgs *__restrict__ tab) {
+// first h.hot labels of the side live in shared memory; the rest ("cold"
+// second endpoints) live in the slot's device memory, either as a dense
+// histogram over the owner's label range (HCOLD = false) or as an
+// open-addressing hash table sized by the owner's bound on distinct second
+// endpoints (HCOLD = true, a few times smaller, so that more slots fit a
+// scratch budget).  A touched list (device memory, counter in shared memory)
+// records each distinct second endpoint once: its label (dense) or its hot
+// offset / table position with the top bit set (hashed).  The second pass sums
+// d - 1 over a segment in registers and adds it to the centre once.
+constexpr uint32_t TCOLD = 0x80000000u;  // touched-list tag of a hash-table position
+
+// Inserts cold second endpoint x2 into the slot's hash table; returns its
+// position and whether it was new.
+__device__ __forceinline__ uint32_t cold_insert(uint32_t *key, uint32_t *val, int lg, uint32_t x2, bool &isnew,
+                                                unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t p = hash_home(x2, lg);
+  for (uint32_t probe = 0;; probe++) {
+    if (probe > mask) { atomicOr(err, 4ull); isnew = false; return TCOLD - 1; }
+    uint32_t k = __ldcg(&key[p]);
+    if (k == EMPTY) k = atomicCAS(&key[p], EMPTY, x2);
+    if (k == EMPTY || k == x2) break;
+    p = (p + 1) & mask;
+  }
+  isnew = atomicAdd(&val[p], 1u) == 0u;
+  return p;
+}
+
+__device__ __forceinline__ uint32_t cold_get(const uint32_t *key, const uint32_t *val, int lg, uint32_t x2,
+                                             unsigned long long *err) {
+  const uint32_t mask = (1u << lg) - 1;
+  uint32_t p = hash_home(x2, lg);
+  for (uint32_t probe = 0; __ldcg(&key[p]) != x2; probe++) {
+    if (probe > mask) { atomicOr(err, 8ull); return 0; }
+    p = (p + 1) & mask;
+  }
+  return __ldcg(&val[p]);
+}
+
+// Shared-memory hot counts: 32-bit, or 16-bit two to a word for owners whose
+// wedge count (and so every group size) is below 2^16.
+template <bool HOT16>
+__device__ __forceinline__ bool hot_inc(uint32_t *hot, uint32_t r) {
+  if (HOT16) {
+    const uint32_t sh = (r & 1u) << 4;
+    return ((atomicAdd(&hot[r >> 1], 1u << sh) >> sh) & 0xffffu) == 0u;
+  }
+  return atomicAdd(&hot[r], 1u) == 0u;
+}
+template <bool HOT16>
+__device__ __forceinline__ uint32_t hot_get(const uint32_t *hot, uint32_t r) {
+  if (HOT16) return (hot[r >> 1] >> ((r & 1u) << 4)) & 0xffffu;
+  return hot[r];
+}
+template <bool HOT16>
+__device__ __forceinline__ void hot_clear(uint32_t *hot, uint32_t r) {
+  // Only this entry's half: the other half of the word may belong to an entry
+  // another thread is still reading (with global counts alone, no barrier
+  // separates the endpoint phase from the reset).
+  if (HOT16) atomicAnd(&hot[r >> 1], (r & 1u) ? 0x0000ffffu : 0xffff0000u);
+  else hot[r] = 0;
+}
+__host__ __device__ constexpr uint32_t hot_words(uint32_t hot, bool hot16) { return hot16 ? (hot + 1) / 2 : hot; }
+
+// Work unit of the one-block kernels: a neighbour's whole segment of second
+// endpoints, or -- when some staged segment is longer than twice the owner's
+// chunk size -- up to that many consecutive endpoints of one segment, so that
+// an owner whose wedges sit in a few long segments (through hub centres)
+// spreads them over all its warps.  The chunk size is the owner's wedges per
+// warp, rounded up to a power of two, at least SEG_CHUNK.
+constexpr uint32_t SEG_CHUNK = 256;
+
+// Chunk j of the staged neighbours: the neighbour k it belongs to (first k
+// with ck[k] > j), the end c of the chunk's range in that segment (its
+// length, capped at the chunk end), the segment's first slot oy and the
+// chunk's first position e_lo.
+template <int NT>
+__device__ __forceinline__ uint32_t seg_chunk(const uint32_t *ck, const uint32_t *cs, const uint32_t *oys, uint32_t j,
+                                              uint32_t ch, uint32_t &c, uint32_t &oy, uint32_t &e_lo) {
+  uint32_t lo = 0, hi = NT - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (ck[mid] > j) hi = mid;
+    else lo = mid + 1;
+  }
+  const uint32_t len = cs[lo];
+  const uint32_t first = ck[lo] - (len + ch - 1) / ch;  // the neighbour's first chunk
+  e_lo = (j - first) * ch;
+  c = e_lo + ch < len ? e_lo + ch : len;
+  oy = oys[lo];
+  return lo;
+}
+
+// The next work unit of a warp: chunk j of the staged neighbours when the
+// segments are split (split != 0), else the whole segment of neighbour j.
+// Returns the neighbour, or NT when the staged work is done.
+template <int NT>
+__device__ __forceinline__ uint32_t next_unit(uint32_t *s_next, const uint32_t *ck, const uint32_t *cs,
+                                              const uint32_t *oys, int split, uint32_t units, uint32_t ch,
+                                              uint32_t &c, uint32_t &oy, uint32_t &e_lo) {
+  uint32_t j = 0;
+  if (lane_id() == 0) j = atomicAdd(s_next, 1u);
+  j = __shfl_sync(FULL, j, 0);
+  if (j >= units) return NT;
+  if (split) return seg_chunk<NT>(ck, cs, oys, j, ch, c, oy, e_lo);
+  c = cs[j];
+  oy = oys[j];
+  e_lo = 0;
+  return j;
+}
+
+// One block of NT threads per owner and slot: the heavy tier (NT = 1024,
+// 32-bit hot counts, cold part dense or hashed) and the medium tier (NT =
+// 256, 16-bit hot counts, cold part hashed).  The owner's neighbours are
+// staged NT at a time, and each warp takes whole neighbours from a shared
+// counter and walks the neighbour's segment of second endpoints with its
+// lanes (coalesced adjacency reads).  Counts of the first h.hot labels of the
+// side live in shared memory; the rest ("cold" second endpoints) live in the
+// slot's device memory, either as a dense histogram over the owner's label
+// range (HCOLD = false) or as an open-addressing hash table sized by the
+// owner's bound on distinct second endpoints (HCOLD = true).  A touched list
+// (device memory, counter in shared memory) records each distinct second
+// endpoint once: its label (dense) or its hot offset / table position with
+// the top bit set (hashed).  The second pass sums d - 1 over a segment in
+// registers and adds it to the centre once.  Owners come from the work queue
+// acc[QUEUE].
+template <bool PV, bool PE, bool MULTI, bool HCOLD, int NT, bool HOT16, int QUEUE>
+__global__ void __launch_bounds__(NT) k_owner(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
+                                              HeavySlots h, const uint64_t *__restrict__ items,
+                                              const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t hb_hot[];
-  __shared__ uint32_t s_c[HB_THREADS], s_oy[HB_THREADS], s_y[HB_THREADS];
-  __shared__ unsigned long long s_hubarr[2 * HUBK];
+  __shared__ uint32_t s_c[NT], s_oy[NT], s_y[NT];
+  __shared__ uint32_t s_ck[NT];  // inclusive prefix of the staged neighbours' chunk counts
+  __shared__ uint32_t s_w[33];
+  __shared__ uint8_t s_nar[NT];  // the neighbour's list takes 32-bit edge partials
+  __shared__ unsigned long long s_hubarr[(PV && !MULTI) ? 2 * HUBK : 1];
   __shared__ uint32_t s_item, s_next, s_nt;
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
   const uint32_t slot = blockIdx.x, tid = threadIdx.x, lane = lane_id();
-  uint32_t *A = h.A + static_cast<size_t>(slot) * h.side;
+  uint32_t *A = HCOLD ? nullptr : h.A + static_cast<size_t>(slot) * h.side;
+  uint32_t *hkey = HCOLD ? h.hkey + static_cast<size_t>(slot) * h.hcap : nullptr;
+  uint32_t *hval = HCOLD ? h.hval + static_cast<size_t>(slot) * h.hcap : nullptr;
   uint32_t *T = h.T + static_cast<size_t>(slot) * h.tcap;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
   if (s_hub) hub_zero(s_hub);
-  for (uint32_t t = tid; t < h.hot; t += HB_THREADS) hb_hot[t] = 0;
+  for (uint32_t t = tid; t < hot_words(h.hot, HOT16); t += NT) hb_hot[t] = 0;
   if (tid == 0) s_nt = 0;
   for (;;) {
-    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[ACC_QHEAVY], 1ull));
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= nlist) break;
@@ -1003,32 +1154,50 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t 
     }
     const uint32_t base = dense_base(a, x1);  // label of histogram entry 0
     const uint32_t xbase = a.off[x1], dp = owner_span(a, x1);
+    const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
+    if (HOT16 && wc > 0xffffu) {  // the tier split guarantees 16-bit counts suffice
+      __syncthreads();            // every thread has read s_item
+      if (tid == 0) atomicOr(err, 16ull);
+      continue;
+    }
+    const int lg = HCOLD ? table_lg(wc, a.n, a.nU, x1, a.rev) : 0;
     // ---- aggregate
-    for (uint32_t s0 = 0; s0 < dp; s0 += HB_THREADS) {
+    uint32_t ch = SEG_CHUNK;
+    while (static_cast<uint64_t>(ch) * (NT / 32) < wc) ch <<= 1;
+    uint32_t units = 0;  // work units of the staged neighbours
+    int split = 0;       // some staged segment is longer than a chunk
+    for (uint32_t s0 = 0; s0 < dp; s0 += NT) {
       {
         uint32_t y, c, oy;
         owner_nbr(a, xbase, s0 + tid, s0 + tid < dp, y, c, oy);
         s_c[tid] = c;
         s_oy[tid] = oy;
         s_y[tid] = y;
+        if (tid == 0) s_next = 0;
+        split = __syncthreads_or(c > 2 * ch);
+        if (split) s_ck[tid] = block_incl_scan((c + ch - 1) / ch, s_w, &units);  // barriers inside
+        else units = dp - s0 < NT ? dp - s0 : NT;
       }
-      if (tid == 0) s_next = 0;
       __syncthreads();
-      const uint32_t nn = dp - s0 < HB_THREADS ? dp - s0 : HB_THREADS;
       for (;;) {
-        uint32_t j = 0;
-        if (lane == 0) j = atomicAdd(&s_next, 1u);
-        j = __shfl_sync(FULL, j, 0);
-        if (j >= nn) break;
-        const uint32_t c = s_c[j], oy = s_oy[j];
-        for (uint32_t e0 = 0; e0 < c; e0 += 32) {
+        uint32_t c, oy, e_lo;
+        if (next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo) == NT) break;
+        for (uint32_t e0 = e_lo; e0 < c; e0 += 32) {
           const bool act = e0 + lane < c;
-          uint32_t x2 = 0;
+          uint32_t tag = 0;
           bool isnew = false;
           if (act) {
-            x2 = a.adj[oy + e0 + lane];
+            const uint32_t x2 = a.adj[oy + e0 + lane];
             const uint32_t r = x2 - base;
-            isnew = (r < h.hot ? atomicAdd(&hb_hot[r], 1u) : atomicAdd(&A[r], 1u)) == 0u;
+            if (r < h.hot) {
+              isnew = hot_inc<HOT16>(hb_hot, r);
+              tag = HCOLD ? r : x2;
+            } else if (HCOLD) {
+              tag = TCOLD | cold_insert(hkey, hval, lg, x2, isnew, err);
+            } else {
+              isnew = atomicAdd(&A[r], 1u) == 0u;
+              tag = x2;
+            }
           }
           const uint32_t bm = __ballot_sync(FULL, isnew);
           if (bm) {
@@ -1037,7 +1206,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t 
             b0 = __shfl_sync(FULL, b0, 0);
             if (isnew) {
               const uint32_t at = b0 + __popc(bm & lanemask_lt());
-              if (at < h.tcap) T[at] = x2;
+              if (at < h.tcap) T[at] = tag;
               else atomicOr(err, 16ull);
             }
           }
@@ -1048,9 +1217,25 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t 
     const uint32_t nt = s_nt < h.tcap ? s_nt : static_cast<uint32_t>(h.tcap);
     // ---- endpoints: C(d, 2) per distinct second endpoint
     unsigned long long own = 0;
-    for (uint32_t t = tid; t < nt; t += HB_THREADS) {
-      const uint32_t x2 = T[t], r = x2 - base;
-      unsigned long long d = r < h.hot ? hb_hot[r] : __ldcg(&A[r]), b = d * (d - 1) / 2;
+    for (uint32_t t = tid; t < nt; t += NT) {
+      const uint32_t v = T[t];
+      uint32_t x2;
+      unsigned long long d;
+      if (HCOLD) {
+        if (v & TCOLD) {
+          const uint32_t p = v & ~TCOLD;
+          x2 = __ldcg(&hkey[p]);
+          d = __ldcg(&hval[p]);
+        } else {
+          x2 = base + v;
+          d = hot_get<HOT16>(hb_hot, v);
+        }
+      } else {
+        x2 = v;
+        const uint32_t r = x2 - base;
+        d = r < h.hot ? hot_get<HOT16>(hb_hot, r) : __ldcg(&A[r]);
+      }
+      const unsigned long long b = d * (d - 1) / 2;
       own += b;
       if (PV && b) pv_add(s_hub, a, x2, b);
     }
@@ -1062,46 +1247,65 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t 
     }
     // ---- centres and edges: d - 1 per wedge
     if (PV || PE) {
-      for (uint32_t s0 = 0; s0 < dp; s0 += HB_THREADS) {
-        if (dp > HB_THREADS) {  // otherwise the first pass's staging is still in place
+      for (uint32_t s0 = 0; s0 < dp; s0 += NT) {
+        {
           uint32_t y, c, oy;
-          owner_nbr(a, xbase, s0 + tid, s0 + tid < dp, y, c, oy);
-          s_c[tid] = c;
-          s_oy[tid] = oy;
-          s_y[tid] = y;
+          const bool v = s0 + tid < dp;
+          owner_nbr(a, xbase, s0 + tid, v, y, c, oy);
+          if (PE) s_nar[tid] = v && es_narrow(a, x1, a.off[y + 1] - a.off[y]);
+          if (tid == 0) s_next = 0;
+          if (dp > NT) {  // otherwise the first pass's staging is still in place
+            s_c[tid] = c;
+            s_oy[tid] = oy;
+            s_y[tid] = y;
+            split = __syncthreads_or(c > 2 * ch);
+            if (split) s_ck[tid] = block_incl_scan((c + ch - 1) / ch, s_w, &units);  // barriers inside
+            else units = dp - s0 < NT ? dp - s0 : NT;
+          }
         }
-        if (tid == 0) s_next = 0;
         __syncthreads();
-        const uint32_t nn = dp - s0 < HB_THREADS ? dp - s0 : HB_THREADS;
         for (;;) {
-          uint32_t j = 0;
-          if (lane == 0) j = atomicAdd(&s_next, 1u);
-          j = __shfl_sync(FULL, j, 0);
-          if (j >= nn) break;
-          const uint32_t c = s_c[j], oy = s_oy[j];
+          uint32_t c, oy, e_lo;
+          const uint32_t k = next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo);
+          if (k == NT) break;
+          const bool nar = PE && s_nar[k];
           unsigned long long sum = 0;
-          for (uint32_t e = lane; e < c; e += 32) {
-            const uint32_t sl = oy + e, r = a.adj[sl] - base;
-            const uint32_t d = r < h.hot ? hb_hot[r] : __ldcg(&A[r]);
+          for (uint32_t e = e_lo + lane; e < c; e += 32) {
+            const uint32_t sl = oy + e, x2 = a.adj[sl], r = x2 - base;
+            uint32_t d;
+            if (r < h.hot) d = hot_get<HOT16>(hb_hot, r);
+            else if (HCOLD) d = cold_get(hkey, hval, lg, x2, err);
+            else d = __ldcg(&A[r]);
             if (d > 1) {
               sum += d - 1;
-              if (PE) atomicAdd(&a.es[sl], static_cast<unsigned long long>(d - 1));
+              if (PE) es_add_wedge(a, sl, d - 1, nar);
             }
           }
           sum = warp_sum(sum);
           if (lane == 0 && sum) {
-            if (PV) pv_add(s_hub, a, s_y[j], sum);
-            if (PE) atomicAdd(&a.es[xbase + s0 + j], sum);
+            if (PV) pv_add(s_hub, a, s_y[k], sum);
+            if (PE) atomicAdd(&a.es[xbase + s0 + k], sum);
           }
         }
         __syncthreads();
       }
     }
     // ---- reset the slot's used entries
-    for (uint32_t t = tid; t < nt; t += HB_THREADS) {
-      const uint32_t r = T[t] - base;
-      if (r < h.hot) hb_hot[r] = 0;
-      else A[r] = 0;
+    for (uint32_t t = tid; t < nt; t += NT) {
+      const uint32_t v = T[t];
+      if (HCOLD) {
+        if (v & TCOLD) {
+          const uint32_t p = v & ~TCOLD;
+          hkey[p] = EMPTY;
+          hval[p] = 0;
+        } else {
+          hot_clear<HOT16>(hb_hot, v);
+        }
+      } else {
+        const uint32_t r = v - base;
+        if (r < h.hot) hot_clear<HOT16>(hb_hot, r);
+        else A[r] = 0;
+      }
     }
     __syncthreads();
     if (tid == 0) s_nt = 0;
@@ -1110,6 +1314,22 @@ __global__ void __launch_bounds__(HB_THREADS) k_heavy1(CArgs a0, const uint32_t 
   __syncthreads();
   if (s_hub) hub_flush(s_hub, a0);
 }
+
+// The heavy tier's instance (1024 threads, 32-bit hot counts, dense or hashed
+// cold part) and the large tier's (MH_THREADS threads, 16-bit hot counts,
+// hashed cold part).
+template <bool PV, bool PE, bool MULTI, bool HCOLD>
+constexpr auto k_heavy1 = k_owner<PV, PE, MULTI, HCOLD, HB_THREADS, false, ACC_QHEAVY>;
+constexpr int MH_THREADS = 256;
+constexpr uint32_t LARGE_LIMIT = 0xffff;  // the large tier's 16-bit counts bound its owners' wedges
+// The large tier is off by default (large_max = med_max): with work split into
+// chunks, the 1024-thread kernel counts owners of 4K-16K wedges as fast as the
+// 256-thread one (20M x 60M: 1420 vs 1425 ms per count) or faster (1M x 4M:
+// 47.8 vs 54.3 ms), on every graph measured.  Pinned plans can still use it.
+constexpr uint32_t LARGE_MAX = MED_MAX;
+constexpr uint32_t MH_HOT = 16384;        // large tier: labels counted in shared memory (16-bit)
+template <bool PV, bool PE, bool MULTI>
+constexpr auto k_large = k_owner<PV, PE, MULTI, true, MH_THREADS, true, ACC_QLARGE>;
 
 // ---------------------------------------------------------------------------
 // Sort aggregation: the wedges of a chunk of first endpoints [lo, hi) are
@@ -1303,22 +1523,27 @@ __global__ void k_chunk_end(const uint64_t *__restrict__ wpre, uint64_t n, uint3
 
 // ---------------------------------------------------------------------------
 // Tier classification.
+// Writes each owner to its tier's list; the lists hold cap[t] entries (the
+// counts of the statistics pass), and an owner past them sets an error bit
+// instead of being written.
+struct TierCaps {
+  uint64_t cap[4];
+};
+
 __global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64_t olo, uint64_t ohi,
-                           uint64_t light_max, uint64_t med_max,
-                           uint64_t hub_min, uint32_t *__restrict__ light, uint32_t *__restrict__ med,
-                           uint64_t *__restrict__ heavy_keys, int bitsN, unsigned long long *acc) {
+                           uint64_t light_max, uint64_t med_max, uint64_t large_max, uint64_t hub_min,
+                           uint32_t *__restrict__ light, uint32_t *__restrict__ med, uint32_t *__restrict__ large,
+                           uint64_t *__restrict__ heavy_keys, int bitsN, unsigned long long *acc, TierCaps caps) {
   size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   size_t iters = (n + stride - 1) / stride;
   for (size_t itn = 0; itn < iters; itn++) {
     size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x + itn * stride;
     uint64_t wc = (x < n && x >= olo && x < ohi) ? wpre[x + 1] - wpre[x] : 0;
-    int tier = wc == 0 ? 0 : (wc <= light_max ? 1 : (wc <= med_max ? 2 : 3));
-    uint32_t hubs = __popc(__ballot_sync(FULL, tier == 3 && wc > hub_min));
+    int tier = wc == 0 ? 0 : (wc <= light_max ? 1 : (wc <= med_max ? 2 : (wc <= large_max ? 3 : 4)));
+    uint32_t hubs = __popc(__ballot_sync(FULL, tier == 4 && wc > hub_min));
     if (lane_id() == 0 && hubs) atomicAdd(&acc[ACC_NHUB], (unsigned long long)hubs);
 #pragma unroll
-    for (int t = 1; t <= 3; t++) {
-      unsigned long long ws = warp_sum(static_cast<unsigned long long>(tier == t ? wc : 0));
-      if (lane_id() == 0 && ws) atomicAdd(&acc[ACC_WLIGHT + t - 1], ws);
+    for (int t = 1; t <= 4; t++) {
       uint32_t bm = __ballot_sync(FULL, tier == t);
       if (!bm) continue;
       uint32_t leader = __ffs(bm) - 1;
@@ -1327,8 +1552,13 @@ __global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64
       b0 = __shfl_sync(FULL, b0, leader);
       if (tier == t) {
         uint64_t at = b0 + __popc(bm & lanemask_lt());
+        if (at >= caps.cap[t - 1]) {
+          atomicOr(&acc[ACC_ERR], 128ull);
+          continue;
+        }
         if (t == 1) light[at] = static_cast<uint32_t>(x);
         else if (t == 2) med[at] = static_cast<uint32_t>(x);
+        else if (t == 3) large[at] = static_cast<uint32_t>(x);
         else {
           // decreasing wedge count first (largest-first scheduling)
           const uint64_t cmax = (uint64_t(1) << (63 - bitsN)) - 1;
@@ -1389,11 +1619,14 @@ __global__ void k_out_vertex(const unsigned long long *__restrict__ pv, const ui
 // Per-edge count of canonical edge e = the sums on its two adjacency slots.
 // Canonical edges are ordered by U endpoint, so slotA reads stay within one
 // list for runs of edges.
-__global__ void k_edge_sums(const unsigned long long *__restrict__ es, const uint32_t *__restrict__ slotA,
-                            const uint32_t *__restrict__ slotB, uint64_t m, uint64_t *__restrict__ E) {
+__global__ void k_edge_sums(const unsigned long long *__restrict__ es, const unsigned int *__restrict__ es32,
+                            const uint32_t *__restrict__ slotA, const uint32_t *__restrict__ slotB, uint64_t m,
+                            uint64_t *__restrict__ E) {
   for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-       e += static_cast<size_t>(gridDim.x) * blockDim.x)
-    E[e] = es[slotA[e]] + es[slotB[e]];
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const uint32_t sa = slotA[e], sb = slotB[e];
+    E[e] = es[sa] + es[sb] + es32[sa] + es32[sb];
+  }
 }
 
 // Input pair k reports the count of its canonical edge.
@@ -1448,60 +1681,278 @@ static int max_clusters(K kernel, unsigned block, unsigned cl, size_t smem) {
   return nc;
 }
 
+// Autotuner statistics of the owners in [olo, ohi) under one owner direction:
+// owners and wedges per tier, the heavy owners' largest wedge count, label
+// range (the length of a dense histogram for them) and distinct bound, the
+// largest wedge count overall, the heavy owners above the hub threshold, and
+// the prefix sums of second-endpoint wedges at the candidate hot-range sizes
+// (wother is the other direction's wedge prefix: a wedge's second endpoint is
+// the owner of that wedge in the other direction).
+constexpr uint32_t HOT_SMALL = 16384, HOT_LARGE = 49152;  // candidate hot-range sizes
+constexpr uint64_t LARGE_LIMIT_D = 0xffff;                 // the large tier's bound (16-bit counts)
+enum { TS_N = 0, TS_W = 4, TS_HMAXW = 8, TS_HRANGE = 9, TS_HDIST = 10, TS_MAXW = 11, TS_NHUB = 12, TS_PRE = 13,
+       TS_SPAN = 17, TS_WMID = 18, TS_WORDS = 20 };
+
+__global__ void k_tier_stats(const uint64_t *__restrict__ wpre, const uint64_t *__restrict__ wother, uint64_t n,
+                             uint32_t nU, int rev, uint64_t olo, uint64_t ohi, uint64_t light_max, uint64_t med_max,
+                             uint64_t large_max, uint64_t hub_min, const uint32_t *__restrict__ off,
+                             const uint32_t *__restrict__ degp, unsigned long long *out) {
+  unsigned long long cnt[4] = {0, 0, 0, 0}, ws[4] = {0, 0, 0, 0}, hmaxw = 0, hrange = 0, hdist = 0, maxw = 0,
+                     nhub = 0, span = 0, wmid = 0;
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const uint64_t wc = wpre[x + 1] - wpre[x];
+    if (wc == 0 || x < olo || x >= ohi) continue;
+    const int t = wc <= light_max ? 0 : (wc <= med_max ? 1 : (wc <= large_max ? 2 : 3));
+    cnt[t]++;
+    ws[t] += wc;
+    maxw = wc > maxw ? wc : maxw;
+    // neighbours of the owners between med_max and the large tier's limit:
+    // their wedges per neighbour (mean segment length) choose the large tier
+    if (wc > med_max && wc <= LARGE_LIMIT_D) {
+      span += rev ? off[x + 1] - off[x] : degp[x];
+      wmid += wc;
+    }
+    if (t == 3) {
+      const uint32_t xl = static_cast<uint32_t>(x);
+      const unsigned long long r = distinct_bound(~0ull, n, nU, xl, rev), d = distinct_bound(wc, n, nU, xl, rev);
+      hmaxw = wc > hmaxw ? wc : hmaxw;
+      hrange = r > hrange ? r : hrange;
+      hdist = d > hdist ? d : hdist;
+      if (wc > hub_min) nhub++;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; t++) {
+    const unsigned long long c = warp_sum(cnt[t]), w = warp_sum(ws[t]);
+    if (lane_id() == 0 && c) {
+      atomicAdd(&out[TS_N + t], c);
+      atomicAdd(&out[TS_W + t], w);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    hmaxw = max(hmaxw, __shfl_xor_sync(FULL, hmaxw, o));
+    hrange = max(hrange, __shfl_xor_sync(FULL, hrange, o));
+    hdist = max(hdist, __shfl_xor_sync(FULL, hdist, o));
+    maxw = max(maxw, __shfl_xor_sync(FULL, maxw, o));
+  }
+  nhub = warp_sum(nhub);
+  span = warp_sum(span);
+  wmid = warp_sum(wmid);
+  if (lane_id() == 0 && span) {
+    atomicAdd(&out[TS_SPAN], span);
+    atomicAdd(&out[TS_WMID], wmid);
+  }
+  if (lane_id() == 0) {
+    if (hmaxw) atomicMax(&out[TS_HMAXW], hmaxw);
+    if (hrange) atomicMax(&out[TS_HRANGE], hrange);
+    if (hdist) atomicMax(&out[TS_HDIST], hdist);
+    if (maxw) atomicMax(&out[TS_MAXW], maxw);
+    if (nhub) atomicAdd(&out[TS_NHUB], nhub);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t nV = n - nU;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const uint64_t H = k == 0 ? HOT_SMALL : HOT_LARGE;
+      const uint64_t hu = H < nU ? H : nU, hv = H < nV ? H : nV;
+      out[TS_PRE + 2 * k] = wother[hu] - wother[0];
+      out[TS_PRE + 2 * k + 1] = wother[nU + hv] - wother[nU];
+    }
+  }
+}
+
+struct TierStats {  // tiers: light, medium, large, heavy
+  uint64_t n[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+  uint64_t hmaxw = 0, hrange = 0, hdist = 0, maxw = 0, nhub = 0;
+  uint64_t pre[4] = {0, 0, 0, 0};
+  uint64_t span_mid = 0, w_mid = 0;  // neighbours and wedges of the owners with med_max < wedges <= LARGE_LIMIT
+};
+
+constexpr uint64_t HUB_MIN = uint64_t(1) << 18;  // owners given a cluster when hubs get one
+constexpr uint64_t HUB_MAX = uint64_t(1) << 20;  // hubs get clusters only past this many wedges
+
+// Statistics into buf (TS_WORDS words of device memory; the graph's own
+// buffer when buf is NULL).  Planning calls that may run while the graph is
+// being counted (pb_autotune, pb_count_bytes) pass a buffer of their own.
+static pb_status tier_stats(pb_graph *g, int rev, uint64_t olo, uint64_t ohi, uint64_t light_max, uint64_t med_max,
+                            uint64_t large_max, cudaStream_t s, TierStats *ts, unsigned long long *buf = nullptr) {
+  if (!buf) {
+    if (!g->tstat) PB_TRY(dalloc_t(&g->tstat, TS_WORDS, s));
+    buf = g->tstat;
+  }
+  PB_CUDA(cudaMemsetAsync(buf, 0, TS_WORDS * sizeof(unsigned long long), s));
+  const uint64_t *wp = rev ? g->wpre_rev : g->wpre, *wo = rev ? g->wpre : g->wpre_rev;
+  k_tier_stats<<<grid_for(g->n, 256, 4096), 256, 0, s>>>(wp, wo, g->n, g->nU, rev, olo, ohi, light_max, med_max,
+                                                        large_max, HUB_MIN, g->off, g->degp, buf);
+  count_launch();
+  unsigned long long h[TS_WORDS];
+  PB_CUDA(cudaMemcpyAsync(h, buf, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PB_CUDA(cudaStreamSynchronize(s));
+  for (int t = 0; t < 4; t++) {
+    ts->n[t] = h[TS_N + t];
+    ts->w[t] = h[TS_W + t];
+  }
+  ts->hmaxw = h[TS_HMAXW];
+  ts->hrange = h[TS_HRANGE];
+  ts->hdist = h[TS_HDIST];
+  ts->maxw = h[TS_MAXW];
+  ts->nhub = h[TS_NHUB];
+  ts->span_mid = h[TS_SPAN];
+  ts->w_mid = h[TS_WMID];
+  for (int k = 0; k < 4; k++) ts->pre[k] = h[TS_PRE + k];
+  return PB_OK;
+}
+
+// Device memory of one heavy slot: a dense histogram over the heavy owners'
+// label range (or a hash table for their cold second endpoints) and a touched
+// list bounded by their distinct second endpoints.
+static uint64_t dense_slot_bytes(const pb_graph *g, const TierStats &ts, uint64_t *side, uint64_t *tcap) {
+  uint64_t sd = g->nU > g->nV ? g->nU : g->nV;
+  if (ts.hrange && ts.hrange < sd) sd = ts.hrange;
+  const uint64_t tc = ts.hdist < sd ? ts.hdist : sd;
+  if (side) *side = sd;
+  if (tcap) *tcap = tc;
+  return (sd + tc) * sizeof(uint32_t);
+}
+
+static uint64_t hash_slot_bytes(const pb_graph *g, const TierStats &ts, uint64_t *hcap, uint64_t *tcap) {
+  uint64_t sd = g->nU > g->nV ? g->nU : g->nV;
+  const uint64_t tc = ts.hdist < sd ? ts.hdist : sd;
+  uint64_t cap = 32;
+  while (cap < 2 * tc) cap <<= 1;
+  if (hcap) *hcap = cap;
+  if (tcap) *tcap = tc;
+  return (2 * cap + tc) * sizeof(uint32_t);
+}
+
+// Resident blocks of the one-block heavy kernel with `hot` shared-memory labels.
+static uint64_t heavy1_resident(int device, uint32_t hot) {
+  int per_sm = 0;
+  const size_t smem = hot * sizeof(uint32_t);
+  cudaFuncSetAttribute(k_heavy1<false, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<false, true, false, false>, HB_THREADS,
+                                                    smem) != cudaSuccess)
+    cudaGetLastError();
+  return static_cast<uint64_t>(sm_count(device)) * (per_sm > 0 ? per_sm : 1);
+}
+
+// Large-tier slot: a hash table for the cold second endpoints of an owner of
+// at most large_max wedges (load at most 1/2) and its touched list.
+static void large_slot_shape(uint64_t large_max, HeavySlots *hm) {
+  uint64_t cap = 32;
+  while (cap < 2 * large_max) cap <<= 1;
+  hm->hcap = cap;
+  hm->tcap = large_max;
+  hm->hot = MH_HOT;
+}
+static uint64_t large_slot_bytes(const HeavySlots &hm) { return (2 * hm.hcap + hm.tcap) * sizeof(uint32_t); }
+
+// The statistics part of the plan: tiers, hot range, and the aggregation that
+// PB_AGG_AUTO uses (rules documented with pb_plan_t).
+static void plan_from_stats(const pb_graph *g, const TierStats &ts, uint64_t budget, pb_plan_t *plan) {
+  for (int t = 0; t < 4; t++) {
+    plan->owners[t] = ts.n[t];
+    plan->wedges[t] = ts.w[t];
+  }
+  plan->max_owner_wedges = ts.maxw;
+  plan->scratch_bytes = budget;
+  plan->mid_segment = ts.span_mid ? static_cast<double>(ts.w_mid) / static_cast<double>(ts.span_mid) : 0.0;
+  const double W = g->W ? static_cast<double>(g->W) : 1.0;
+  const double hit16 = static_cast<double>(ts.pre[0] + ts.pre[1]) / W;
+  const double hit48 = static_cast<double>(ts.pre[2] + ts.pre[3]) / W;
+  plan->hot = hit16 < 0.9 ? HOT_LARGE : HOT_SMALL;
+  plan->hot_hit = plan->hot == HOT_LARGE ? hit48 : hit16;
+  const uint64_t nh = ts.n[3];
+  plan->hub_min = UINT64_MAX;
+  plan->hub_cluster = 1;
+  plan->heavy_slots = 0;
+  plan->slot_bytes = 0;
+  if (nh == 0) {
+    plan->agg = PB_AGG_BATCH;
+    return;
+  }
+  const uint64_t resident = heavy1_resident(g->device, plan->hot);
+  const uint64_t want = nh < resident ? nh : resident;
+  const uint64_t dslot = dense_slot_bytes(g, ts, nullptr, nullptr), hslot = hash_slot_bytes(g, ts, nullptr, nullptr);
+  const uint64_t fit_d = budget / (dslot + 16), fit_h = budget / (hslot + 16);
+  plan->slot_bytes_dense = dslot;
+  plan->slot_bytes_hash = hslot;
+  plan->resident_blocks = static_cast<uint32_t>(resident);
+  if (ts.hmaxw > HUB_MAX && ts.hmaxw * want > 8 * ts.w[3]) {
+    // one owner would hold a block far past the others: hubs share a cluster
+    plan->agg = PB_AGG_HIST;
+    plan->hub_min = HUB_MIN;
+    plan->hub_cluster = 2;
+    plan->slot_bytes = dslot;
+    plan->heavy_slots = static_cast<uint32_t>(fit_d < want ? fit_d : want);
+  } else if (fit_d >= want || fit_d >= fit_h) {
+    plan->agg = PB_AGG_BATCH;
+    plan->slot_bytes = dslot;
+    plan->heavy_slots = static_cast<uint32_t>(fit_d < want ? fit_d : want);
+  } else {
+    plan->agg = PB_AGG_HASH;
+    plan->slot_bytes = hslot;
+    plan->heavy_slots = static_cast<uint32_t>(fit_h < want ? fit_h : want);
+  }
+}
+
+// What one count runs: the tier bounds, and the heavy tier's path.
 struct Plan {
-  int agg;
   bool pv, pe;
-  uint64_t light_max, med_max;
-  bool dense;         // heavy tier uses dense histograms
-  unsigned cluster;   // blocks per heavy first endpoint
-  uint64_t max_slots; // cap on concurrently processed hubs (0 = resident clusters)
-  uint64_t hub_min;   // heavy first endpoints above this many wedges get a cluster each
+  uint64_t light_max, med_max, large_max;
+  int heavy;          // PB_AGG_HIST / PB_AGG_BATCH: dense; PB_AGG_HASH: hashed
+  uint32_t hot;       // shared-memory labels of the one-block heavy kernel
+  unsigned cluster;   // blocks per hub owner (1: no hub clusters)
   uint64_t owner_lo, owner_hi;  // owners counted
 };
 
-// Tuning knobs (environment): PB_HEAVY_CLUSTER, PB_HEAVY_SLOTS, PB_HUB_MIN.
-static uint64_t env_u64(const char *name, uint64_t dflt) {
-  const char *v = getenv(name);
-  if (!v || !*v) return dflt;
-  return strtoull(v, nullptr, 10);
-}
-
 template <bool PV, bool PE>
-static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t budget, cudaStream_t s) {
+static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, const TierStats &ts, uint64_t budget,
+                           cudaStream_t s) {
   const uint64_t n = g->n;
-  unsigned long long hcnt[ACC_WORDS] = {0};
-  uint32_t *light = nullptr, *med = nullptr, *heavy = nullptr;
+  uint32_t *light = nullptr, *med = nullptr, *large = nullptr, *heavy = nullptr;
   uint64_t *hkeys = nullptr;
-  unsigned long long *dmx = nullptr;
   pb_status st = PB_OK;
   const int sms = sm_count(g->device);
+  // Every launch below is sized from the statistics read before the count, so
+  // the host does not wait on the device again until the outputs are ready.
+  const uint32_t nl = static_cast<uint32_t>(ts.n[0]), nm = static_cast<uint32_t>(ts.n[1]),
+                 nq = static_cast<uint32_t>(ts.n[2]), nh = static_cast<uint32_t>(ts.n[3]);
+  // The persistent tier kernels take this share of the device's resident
+  // blocks (pb_set_grid_share): concurrent counts on other streams then run
+  // side by side instead of waiting for a kernel that holds every SM.
+  auto share = [&](uint64_t resident) -> uint64_t {
+    const double f = g->grid_share > 0.0 && g->grid_share < 1.0 ? g->grid_share : 1.0;
+    const uint64_t r = static_cast<uint64_t>(std::ceil(f * static_cast<double>(resident)));
+    return r < 1 ? 1 : r;
+  };
   do {
-    if ((st = dalloc_t(&light, n + 1, s)) != PB_OK) break;
-    if ((st = dalloc_t(&med, n + 1, s)) != PB_OK) break;
-    if ((st = dalloc_t(&hkeys, n + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&light, nl + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&med, nm + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&large, nq + 1, s)) != PB_OK) break;
+    if ((st = dalloc_t(&hkeys, nh + 1, s)) != PB_OK) break;
     {
       PhaseScope ph(PB_PHASE_CLASSIFY, s);
+      const TierCaps caps = {{nl, nm, nq, nh}};
       k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, p.owner_lo, p.owner_hi, p.light_max, p.med_max,
-                                                        p.hub_min, light, med,
-                                                        hkeys, g->bitsN, a.acc);
+                                                        p.large_max, HUB_MIN, light, med, large, hkeys, g->bitsN,
+                                                        a.acc, caps);
       count_launch();
       ph.finish(s);
     }
-    if (cudaMemcpyAsync(hcnt, a.acc, sizeof(hcnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "tier readback: %s", cudaGetErrorString(cudaGetLastError())); break; }
-    const uint32_t nl = static_cast<uint32_t>(hcnt[ACC_NLIGHT]), nm = static_cast<uint32_t>(hcnt[ACC_NMED]),
-                   nh = static_cast<uint32_t>(hcnt[ACC_NHEAVY]);
     if (nl) {
       PhaseScope ph(PB_PHASE_LIGHT, s);
       const size_t smem = LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t);
       PB_CUDA(cudaFuncSetAttribute(k_light<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_light<PV, PE, false>, LW_THREADS, smem);
-      unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
+      unsigned grid = static_cast<unsigned>(share(static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1)));
       unsigned need = (nl + LW_WARPS - 1) / LW_WARPS;
       PB_LAUNCH((k_light<PV, PE, false>), grid < need ? grid : need, LW_THREADS, smem, s, a, light, nl,
                 (const uint64_t *)nullptr, (const CArgs *)nullptr);
-      ph.finish(s, hcnt[ACC_WLIGHT]);
+      ph.finish(s, ts.w[0]);
     }
     if (nm) {
       PhaseScope ph(PB_PHASE_MEDIUM, s);
@@ -1509,57 +1960,61 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
       PB_CUDA(cudaFuncSetAttribute(k_medium<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_medium<PV, PE, false>, MB_THREADS, smem);
-      unsigned grid = static_cast<unsigned>(sms * (per_sm > 0 ? per_sm : 1));
+      unsigned grid = static_cast<unsigned>(share(static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1)));
       PB_LAUNCH((k_medium<PV, PE, false>), grid < nm ? grid : nm, MB_THREADS, smem, s, a, med, nm,
                 (const uint64_t *)nullptr, (const CArgs *)nullptr);
-      ph.finish(s, hcnt[ACC_WMED]);
+      ph.finish(s, ts.w[1]);
+    }
+    if (nq) {
+      // One MH_THREADS block per owner: 16-bit counts of the first MH_HOT
+      // labels in shared memory, the rest in a small hash table per slot.
+      PhaseScope ph(PB_PHASE_LARGE, s);
+      HeavySlots hm = {};
+      large_slot_shape(p.large_max, &hm);
+      const size_t smem = hot_words(hm.hot, true) * sizeof(uint32_t);
+      auto kern = k_large<PV, PE, false>;
+      PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MH_THREADS, smem);
+      uint64_t nslots = share(static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1));
+      if (nslots > nq) nslots = nq;
+      if ((st = ensure_scratch2(g, nslots * large_slot_bytes(hm), s)) != PB_OK) break;
+      hm.hkey = static_cast<uint32_t *>(g->scratch2);
+      hm.hval = hm.hkey + nslots * hm.hcap;
+      hm.T = hm.hval + nslots * hm.hcap;
+      if (cudaMemsetAsync(hm.hkey, 0xff, nslots * hm.hcap * sizeof(uint32_t), s) != cudaSuccess ||
+          cudaMemsetAsync(hm.hval, 0, nslots * hm.hcap * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
+      PB_LAUNCH(kern, static_cast<unsigned>(nslots), MH_THREADS, smem, s, a, large, nq, hm, (const uint64_t *)nullptr,
+                (const CArgs *)nullptr);
+      ph.finish(s, ts.w[2]);
     }
     if (nh) {
       if ((st = radix_sort(hkeys, nullptr, nh, 64 - 1, s)) != PB_OK) break;
       if ((st = dalloc_t(&heavy, nh, s)) != PB_OK) break;
       k_keys_low<<<grid_for(nh, 256, 4096), 256, 0, s>>>(hkeys, nh, g->bitsN, heavy);
       count_launch();
-      if ((st = dalloc_t(&dmx, 2, s)) != PB_OK) break;
-      if (cudaMemsetAsync(dmx, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-      k_max_wedges_list<<<grid_for(nh, 256, 4096), 256, 0, s>>>(heavy, nh, a.wpre, n, g->nU, a.rev, dmx);
-      count_launch();
-      unsigned long long hdm2[2] = {0, 0};
-      if (cudaMemcpyAsync(hdm2, dmx, sizeof(hdm2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "heavy readback"); break; }
-      const unsigned long long hdm = hdm2[0];
+      const bool hashed = p.heavy == PB_AGG_HASH;
       HeavySlots hs = {};
-      hs.side = g->nU > g->nV ? g->nU : g->nV;
-      if (hdm2[1] && hdm2[1] < hs.side) hs.side = hdm2[1];  // dense histograms span the owners' label ranges
-      size_t slot_bytes;
-      if (p.dense) {
-        hs.tcap = hdm < hs.side ? hdm : hs.side;
-        slot_bytes = (hs.side + hs.tcap) * sizeof(uint32_t);
-      } else {
-        uint64_t cap = 32;
-        while (cap < 2 * hdm) cap <<= 1;
-        hs.hcap = cap;
-        slot_bytes = 2 * cap * sizeof(uint32_t);
-      }
-      auto kern = p.dense ? k_heavy<PV, PE, true, false> : k_heavy<PV, PE, false, false>;
-      // Hubs (wedges > hub_min, the head of the largest-first list) get one
-      // cluster each; the rest one block each (plain batching).
-      uint32_t nhub = p.cluster > 1 ? static_cast<uint32_t>(hcnt[ACC_NHUB]) : 0;
+      uint64_t slot_bytes = hashed ? hash_slot_bytes(g, ts, &hs.hcap, &hs.tcap)
+                                   : dense_slot_bytes(g, ts, &hs.side, &hs.tcap);
+      // Hubs (the head of the largest-first list) get one cluster each; the
+      // rest one block each.
+      const uint32_t nhub = p.cluster > 1 ? static_cast<uint32_t>(ts.nhub) : 0;
       unsigned hub_cl = p.cluster, rest_cl = 1;
-      uint64_t fit = budget / (slot_bytes + 16);
+      const uint64_t fit = budget / (slot_bytes + 16);
       if (fit == 0) { st = fail(PB_ERR_SCRATCH, "scratch budget %llu B below one heavy slot (%llu B)", (unsigned long long)budget, (unsigned long long)slot_bytes); break; }
-      {
-        // When the budget holds fewer slots than there are resident blocks,
-        // every slot is shared by a cluster of blocks so that all SMs work.
+      // The one-block kernel (shared-memory hot range) serves the non-hub
+      // owners when at least one slot per SM fits the budget; otherwise
+      // slots are shared by clusters of blocks so that every SM works.
+      if (fit < static_cast<uint64_t>(sms)) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy<PV, PE, true, false>, HB_THREADS, 0);
         const uint64_t resident = static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1);
-        if (fit < resident) {
-          uint64_t want = (resident + fit - 1) / fit;
-          unsigned c = 1;
-          while (c < want && c < 8) c <<= 1;
-          rest_cl = c;
-          if (hub_cl < c) hub_cl = c;
-        }
+        uint64_t want = (resident + fit - 1) / fit;
+        unsigned c = 1;
+        while (c < want && c < 8) c <<= 1;
+        rest_cl = c;
+        if (hub_cl < c) hub_cl = c;
       }
       struct Part { const uint32_t *list; uint32_t cnt; unsigned cl; };
       Part parts[2] = {{heavy, nhub, hub_cl}, {heavy + nhub, nh - nhub, rest_cl}};
@@ -1567,32 +2022,31 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
       for (const Part &pt : parts) {
         if (pt.cnt == 0) continue;
         const unsigned cl = pt.cl;
-        if (cl > 8) PB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        // A slot processed by one block keeps the counts of the first HB_HOT
-        // labels of the side in shared memory (dense mode).
-        const bool one = p.dense && cl == 1;  // one block per dense slot: k_heavy1
-        const uint32_t hot = one ? HB_HOT : 0;
-        const size_t hsmem = hot * sizeof(uint32_t);
-        hs.hot = hot;
+        const bool one = cl == 1;  // one block per slot: k_heavy1 with the hot range
+        auto ckern = hashed ? k_heavy<PV, PE, false, false> : k_heavy<PV, PE, true, false>;
+        auto okern = hashed ? k_heavy1<PV, PE, false, true> : k_heavy1<PV, PE, false, false>;
+        if (cl > 8) PB_CUDA(cudaFuncSetAttribute(ckern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        hs.hot = one ? p.hot : 0;
+        const size_t hsmem = hs.hot * sizeof(uint32_t);
         int nc = 0;
         if (one) {
-          PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, PE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)hsmem));
+          PB_CUDA(cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
           int per_sm = 0;
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<PV, PE, false>, HB_THREADS, hsmem);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, HB_THREADS, hsmem);
           nc = sms * (per_sm > 0 ? per_sm : 1);
         } else {
-          nc = max_clusters(kern, HB_THREADS, cl, hsmem);
+          nc = max_clusters(ckern, HB_THREADS, cl, hsmem);
         }
         if (nc <= 0) nc = sms / static_cast<int>(cl);
-        uint64_t nslots = static_cast<uint64_t>(nc);
-        if (&pt == &parts[0] && p.max_slots && nslots > p.max_slots) nslots = p.max_slots;
+        uint64_t nslots = share(static_cast<uint64_t>(nc));
         if (nslots > fit) nslots = fit;
         if (nslots > pt.cnt) nslots = pt.cnt;
+        // the touched list is used by k_heavy1 in both modes, by k_heavy in dense mode
+        const uint64_t tlist = (one || !hashed) ? hs.tcap : 0;
         size_t need = nslots * slot_bytes + nslots * 3 * sizeof(uint32_t) + 64;
         if ((st = ensure_scratch(g, need, s)) != PB_OK) break;
         char *sp = static_cast<char *>(g->scratch);
-        if (p.dense) {
+        if (!hashed) {
           hs.A = reinterpret_cast<uint32_t *>(sp);
           hs.T = hs.A + nslots * hs.side;
           hs.tcnt = hs.T + nslots * hs.tcap;
@@ -1600,7 +2054,8 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         } else {
           hs.hkey = reinterpret_cast<uint32_t *>(sp);
           hs.hval = hs.hkey + nslots * hs.hcap;
-          hs.tcnt = hs.hval + nslots * hs.hcap;
+          hs.T = hs.hval + nslots * hs.hcap;
+          hs.tcnt = hs.T + nslots * tlist;
           if (cudaMemsetAsync(hs.hkey, 0xff, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess ||
               cudaMemsetAsync(hs.hval, 0, nslots * hs.hcap * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         }
@@ -1608,18 +2063,18 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, uint64_t 
         if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         if (one) {
-          PB_LAUNCH((k_heavy1<PV, PE, false>), static_cast<unsigned>(nslots), HB_THREADS, hsmem, s, a, pt.list, pt.cnt,
-                    hs, (const uint64_t *)nullptr, (const CArgs *)nullptr);
-        } else if ((st = launch_cluster(kern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list,
+          PB_LAUNCH(okern, static_cast<unsigned>(nslots), HB_THREADS, hsmem, s, a, pt.list, pt.cnt, hs,
+                    (const uint64_t *)nullptr, (const CArgs *)nullptr);
+        } else if ((st = launch_cluster(ckern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list,
                                         pt.cnt, hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) {
           break;
         }
       }
       if (st != PB_OK) break;
-      ph.finish(s, hcnt[ACC_WHEAVY]);
+      ph.finish(s, ts.w[3]);
     }
   } while (0);
-  dfree(light, s); dfree(med, s); dfree(heavy, s); dfree(hkeys, s); dfree(dmx, s);
+  dfree(light, s); dfree(med, s); dfree(large, s); dfree(heavy, s); dfree(hkeys, s);
   return st;
 }
 
@@ -1805,42 +2260,33 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
   if (want_pe) {
     if (!g->es) PB_TRY(dalloc_t(&g->es, na + 1, s));
     PB_CUDA(cudaMemsetAsync(g->es, 0, (na + 1) * sizeof(uint64_t), s));
+    if (!g->es32) PB_TRY(dalloc_t(&g->es32, na + 1, s));
+    PB_CUDA(cudaMemsetAsync(g->es32, 0, (na + 1) * sizeof(uint32_t), s));
   }
   CArgs a;
   // Owner of each wedge: its lower-ranked endpoint (Algorithm 2) or, with the
   // cache optimisation, its higher-ranked one.  Same wedges either way.
   pb_plan_t plan;
-  make_plan(g, &plan);
+  if (g->has_plan) plan = g->plan;  // pinned by pb_set_plan
+  else make_plan_basic(g, &plan);
   a.rev = g->retrieval == PB_RETRIEVE_AUTO ? plan.retrieval == PB_RETRIEVE_HIGH : g->retrieval == PB_RETRIEVE_HIGH;
   a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.n = n;
   a.wpre = a.rev ? g->wpre_rev : g->wpre;
   a.nU = g->nU;
   a.pv = want_pv ? reinterpret_cast<unsigned long long *>(g->pv) : nullptr;
   a.es = want_pe ? reinterpret_cast<unsigned long long *>(g->es) : nullptr;
+  a.es32 = want_pe ? reinterpret_cast<unsigned int *>(g->es32) : nullptr;
+  // y's list takes 32-bit partials when (deg(y) - 1)(largest degree on the
+  // entries' side - 1) stays within 32 bits
+  a.nlim[0] = g->maxdegU > 1 ? static_cast<uint32_t>(0xffffffffull / (g->maxdegU - 1)) : 0xffffffffu;
+  a.nlim[1] = g->maxdegV > 1 ? static_cast<uint32_t>(0xffffffffull / (g->maxdegV - 1)) : 0xffffffffu;
   a.acc = g->acc;
   if (g->W > 0) {
     Plan p;
-    p.agg = agg;
     p.pv = want_pv;
     p.pe = want_pe;
-    p.light_max = LIGHT_MAX;
-    p.med_max = MED_MAX;
     p.owner_lo = o.owner_lo < n ? o.owner_lo : n;
     p.owner_hi = o.owner_hi < n ? o.owner_hi : n;
-    p.dense = agg != PB_AGG_HASH;
-    p.cluster = static_cast<unsigned>(env_u64("PB_HEAVY_CLUSTER", plan.hub_cluster));
-    p.max_slots = env_u64("PB_HEAVY_SLOTS", 0);
-    p.hub_min = env_u64("PB_HUB_MIN", plan.hub_min);
-    if (agg == PB_AGG_BATCH) {
-      // One dense array per concurrently processed heavy first endpoint, no
-      // clusters; first endpoints with at most MED_MAX wedges keep the
-      // shared-memory tiers (a dense array each would exhaust the budget).
-      p.cluster = 1;
-      p.max_slots = 0;
-      p.hub_min = UINT64_MAX;
-    }
-    if (p.cluster < 1) p.cluster = 1;
-    if (p.cluster > 16) p.cluster = 16;
     pb_status st;
     if (agg == PB_AGG_SORT) {
       PhaseScope ph(PB_PHASE_SORT, s);
@@ -1856,10 +2302,33 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
                 : run_sort<false, true, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
       else st = run_sort<false, false, false>(g, a, budget, p.owner_lo, p.owner_hi, s);
       if (st == PB_OK) ph.finish(s, g->W);
-    } else if (want_pv && want_pe) st = run_tiers<true, true>(g, a, p, budget, s);
-    else if (want_pv) st = run_tiers<true, false>(g, a, p, budget, s);
-    else if (want_pe) st = run_tiers<false, true>(g, a, p, budget, s);
-    else st = run_tiers<false, false>(g, a, p, budget, s);
+    } else {
+      // The plan's tier bounds; the statistics under them (one readback, the
+      // only host wait before the outputs); the rest of the plan from them
+      // unless one is pinned.
+      p.light_max = plan.light_max;
+      p.med_max = plan.med_max;
+      p.large_max = plan.large_max;
+      TierStats ts;
+      PB_TRY(tier_stats(g, a.rev, p.owner_lo, p.owner_hi, p.light_max, p.med_max, p.large_max, s, &ts));
+      if (!g->has_plan) plan_from_stats(g, ts, budget, &plan);
+      p.hot = plan.hot;
+      const int heavy = agg == PB_AGG_AUTO ? plan.agg : agg;
+      p.heavy = heavy;
+      p.cluster = 1;
+      if (heavy == PB_AGG_HIST) {
+        // HIST gives hubs a cluster: the pinned or planned size, else two
+        // blocks once the largest owner passes HUB_MAX wedges
+        if (agg == PB_AGG_AUTO) p.cluster = plan.hub_cluster;
+        else if (ts.hmaxw > HUB_MAX) p.cluster = 2;
+      }
+      if (p.cluster < 1) p.cluster = 1;
+      if (p.cluster > 16) p.cluster = 16;
+      if (want_pv && want_pe) st = run_tiers<true, true>(g, a, p, ts, budget, s);
+      else if (want_pv) st = run_tiers<true, false>(g, a, p, ts, budget, s);
+      else if (want_pe) st = run_tiers<false, true>(g, a, p, ts, budget, s);
+      else st = run_tiers<false, false>(g, a, p, ts, budget, s);
+    }
     PB_TRY(st);
   }
   unsigned long long hacc[ACC_WORDS] = {0};
@@ -1884,7 +2353,8 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
   if (want_pe && g->m_in) {
     st = dalloc_t(&Ecan, g->m + 1, s);
     if (st == PB_OK) {
-      k_edge_sums<<<grid_for(g->m, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->es), g->slotA,
+      k_edge_sums<<<grid_for(g->m, 256, 8192), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(g->es),
+                                                            reinterpret_cast<unsigned int *>(g->es32), g->slotA,
                                                             g->slotB, g->m, Ecan);
       count_launch();
       k_out_edge<<<grid_for(g->m_in, 256, 8192), 256, 0, s>>>(Ecan, g->in2c, g->m_in, dE);
@@ -1916,8 +2386,10 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
 namespace pb {
 
 // ---------------------------------------------------------------------------
-// Autotuner (rules from degree and wedge statistics).
-void make_plan(const pb_graph *g, pb_plan_t *plan) {
+// Autotuner (rules from degree and wedge statistics).  The part that needs no
+// device pass: ranking recommendation, owner direction, default tiers.
+void make_plan_basic(const pb_graph *g, pb_plan_t *plan) {
+  *plan = pb_plan_t{};
   const uint64_t w_side = g->w_side_U < g->w_side_V ? g->w_side_U : g->w_side_V;
   plan->W_side = w_side;
   plan->W_rank = g->W;
@@ -1928,16 +2400,32 @@ void make_plan(const pb_graph *g, pb_plan_t *plan) {
   const bool high = g->maxw_rev <= g->maxw;
   plan->retrieval = high ? PB_RETRIEVE_HIGH : PB_RETRIEVE_LOW;
   plan->max_owner_wedges = high ? g->maxw_rev : g->maxw;
-  plan->agg = PB_AGG_AUTO;
-  // owners past 2^20 wedges would keep one block busy for milliseconds:
-  // give owners past 2^18 a pair of blocks
-  if (plan->max_owner_wedges > (uint64_t(1) << 20)) {
-    plan->hub_min = uint64_t(1) << 18;
-    plan->hub_cluster = 2;
-  } else {
-    plan->hub_min = UINT64_MAX;
-    plan->hub_cluster = 1;
+  plan->agg = PB_AGG_BATCH;
+  plan->light_max = LIGHT_MAX;
+  plan->med_max = MED_MAX;
+  plan->large_max = LARGE_MAX;
+  plan->hot = HOT_SMALL;
+  plan->hub_min = UINT64_MAX;
+  plan->hub_cluster = 1;
+}
+
+// The whole plan (pb_autotune): the basic part, then the statistics of the
+// owners under the chosen direction.
+pb_status make_plan(pb_graph *g, uint64_t budget, cudaStream_t s, pb_plan_t *plan) {
+  make_plan_basic(g, plan);
+  if (g->W == 0) {
+    plan->scratch_bytes = budget;
+    return PB_OK;
   }
+  TierStats ts;
+  unsigned long long *buf = nullptr;
+  PB_TRY(dalloc_t(&buf, TS_WORDS, s));
+  const pb_status st = tier_stats(g, plan->retrieval == PB_RETRIEVE_HIGH, 0, g->n, plan->light_max, plan->med_max,
+                                  plan->large_max, s, &ts, buf);
+  dfree(buf, s);
+  PB_TRY(st);
+  plan_from_stats(g, ts, budget, plan);
+  return PB_OK;
 }
 
 }  // namespace pb
@@ -1955,11 +2443,14 @@ struct pb_batch {
   unsigned long long *bacc = nullptr;     // [ACC_WORDS] batch work queues
   unsigned long long *pvbuf = nullptr;    // per-vertex counts, all graphs
   uint64_t pv_total = 0;
-  uint64_t *light = nullptr, *med = nullptr, *heavy = nullptr;
-  uint32_t nl = 0, nm = 0, nh = 0;
-  pb::HeavySlots hs = {};
-  void *scratch = nullptr;
-  uint64_t nslots = 0, slot_bytes = 0;
+  uint64_t *light = nullptr, *med = nullptr, *large = nullptr, *heavy = nullptr, *heavy_h = nullptr;
+  uint32_t nl = 0, nm = 0, nq = 0, nh = 0, nhh = 0;  // nh: dense heavy owners, nhh: hashed heavy owners
+  pb::HeavySlots hs = {}, hsh = {};          // dense and hashed heavy slots
+  void *scratch = nullptr, *scratch_h = nullptr, *scratch_m = nullptr;
+  pb::HeavySlots hsm = {};                   // large-tier slots
+  uint64_t nslots_m = 0;
+  uint64_t nslots = 0, slot_bytes = 0, nslots_h = 0, slot_bytes_h = 0;
+  std::vector<int32_t> agg;                  // per graph: the heavy path its plan chose
   uint64_t W = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1979,7 +2470,8 @@ static void batch_release(pb_batch *b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   cudaStream_t s = 0;
   dfree(b->tab, s); dfree(b->acc, s); dfree(b->bacc, s); dfree(b->pvbuf, s);
-  dfree(b->light, s); dfree(b->med, s); dfree(b->heavy, s); dfree(b->scratch, s);
+  dfree(b->light, s); dfree(b->med, s); dfree(b->large, s); dfree(b->heavy, s); dfree(b->scratch, s);
+  dfree(b->heavy_h, s); dfree(b->scratch_h, s); dfree(b->scratch_m, s);
   cudaStreamSynchronize(s);
   cudaGetLastError();
   delete b;
@@ -2008,8 +2500,12 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
                                (int)(LW_WARPS * (LW_CAP + LW_CAP / 2) * sizeof(uint32_t))));
   PB_CUDA(cudaFuncSetAttribute(k_medium<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)MB_SMEM));
-  PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PB_CUDA(cudaFuncSetAttribute(k_large<PV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(hot_words(MH_HOT, true) * sizeof(uint32_t))));
+  PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(b->hs.hot * sizeof(uint32_t))));
+  PB_CUDA(cudaFuncSetAttribute(k_heavy1<PV, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(b->hsh.hot * sizeof(uint32_t))));
   PB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   pb_status st = PB_OK;
   do {
@@ -2042,14 +2538,40 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
       e1 = cudaGetLastError();
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch medium launch", __FILE__, __LINE__); break; }
     }
+    if (b->nq) {
+      const size_t hb = b->nslots_m * b->hsm.hcap * sizeof(uint32_t);
+      e1 = cudaMemsetAsync(b->hsm.hkey, 0xff, hb, s);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->hsm.hval, 0, hb, s);
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (large slots)", __FILE__, __LINE__); break; }
+      k_large<PV, false, true><<<static_cast<unsigned>(b->nslots_m), MH_THREADS,
+                                 hot_words(MH_HOT, true) * sizeof(uint32_t), s>>>(a0, nullptr, b->nq, b->hsm, b->large,
+                                                                                   b->tab);
+      count_launch();
+      e1 = cudaGetLastError();
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch large launch", __FILE__, __LINE__); break; }
+    }
     if (b->nh) {
       e1 = cudaMemsetAsync(b->scratch, 0, b->nslots * b->slot_bytes + b->nslots * 7 * sizeof(uint32_t) + 64, s);
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (slots)", __FILE__, __LINE__); break; }
-      k_heavy1<PV, false, true><<<static_cast<unsigned>(b->nslots), HB_THREADS, b->hs.hot * sizeof(uint32_t), s>>>(
-          a0, nullptr, b->nh, b->hs, b->heavy, b->tab);
+      k_heavy1<PV, false, true, false><<<static_cast<unsigned>(b->nslots), HB_THREADS, b->hs.hot * sizeof(uint32_t),
+                                         s>>>(a0, nullptr, b->nh, b->hs, b->heavy, b->tab);
       count_launch();
       e1 = cudaGetLastError();
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch heavy launch", __FILE__, __LINE__); break; }
+    }
+    if (b->nhh) {  // graphs whose plan hashes the heavy owners' cold endpoints: own slots, own queue
+      const size_t hb = b->nslots_h * b->hsh.hcap * sizeof(uint32_t);
+      e1 = cudaMemsetAsync(b->hsh.hkey, 0xff, hb, s);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->hsh.hval, 0, hb, s);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->hsh.tcnt, 0, 3 * b->nslots_h * sizeof(uint32_t), s);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->bacc + ACC_QHEAVY, 0, sizeof(unsigned long long), s);
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (hashed slots)", __FILE__, __LINE__); break; }
+      k_heavy1<PV, false, true, true><<<static_cast<unsigned>(b->nslots_h), HB_THREADS,
+                                        b->hsh.hot * sizeof(uint32_t), s>>>(a0, nullptr, b->nhh, b->hsh, b->heavy_h,
+                                                                            b->tab);
+      count_launch();
+      e1 = cudaGetLastError();
+      if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch hashed heavy launch", __FILE__, __LINE__); break; }
     }
   } while (0);
   cudaGraph_t graph = nullptr;
@@ -2069,6 +2591,7 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
   // per-graph argument table and output buffers
   std::vector<CArgs> host_tab(ng);
   b->pv_off.resize(ng);
+  b->agg.assign(ng, PB_AGG_BATCH);
   uint64_t total_n = 0, max_side = 1;
   for (uint32_t i = 0; i < ng; i++) {
     pb_graph *g = b->graphs[i];
@@ -2083,76 +2606,110 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
   PB_TRY(dalloc_t(&b->pvbuf, total_n + 1, s));
   PB_TRY(dalloc_t(&b->light, total_n + 1, s));
   PB_TRY(dalloc_t(&b->med, total_n + 1, s));
+  PB_TRY(dalloc_t(&b->large, total_n + 1, s));
   PB_TRY(dalloc_t(&b->heavy, total_n + 1, s));
-  uint32_t *tl = nullptr, *tm = nullptr;
+  PB_TRY(dalloc_t(&b->heavy_h, total_n + 1, s));
+  uint32_t *tl = nullptr, *tm = nullptr, *tq = nullptr;
   uint64_t *th = nullptr;
   unsigned long long *tacc = nullptr;
   pb_status st = PB_OK;
-  uint64_t max_bound = 1, max_room = 1;
+  // slot sizes over the graphs of each heavy path
+  TierStats dmax, hmax;
+  uint64_t large_max_all = 1;
   do {
     if ((st = dalloc_t(&tacc, ACC_WORDS, s)) != PB_OK) break;
     for (uint32_t i = 0; i < ng && st == PB_OK; i++) {
       pb_graph *g = b->graphs[i];
+      // Each graph's own plan: owner direction, tier bounds and heavy path
+      // from its statistics (or the plan pinned on it).
       pb_plan_t plan;
-      make_plan(g, &plan);
+      if (g->has_plan) plan = g->plan;
+      else make_plan_basic(g, &plan);
       CArgs &a = host_tab[i];
       a.rev = g->retrieval == PB_RETRIEVE_AUTO ? plan.retrieval == PB_RETRIEVE_HIGH : g->retrieval == PB_RETRIEVE_HIGH;
       a.off = g->off; a.adj = g->adj; a.cpos = g->cpos; a.degp = g->degp; a.n = g->n; a.nU = g->nU;
       a.wpre = a.rev ? g->wpre_rev : g->wpre;
       a.pv = b->pv ? b->pvbuf + b->pv_off[i] : nullptr;
       a.es = nullptr;
+      a.es32 = nullptr;
+      a.nlim[0] = a.nlim[1] = 0;
       a.acc = b->acc + static_cast<size_t>(i) * ACC_WORDS;
       b->W += g->W;
       if (g->W == 0) continue;
       const uint64_t n = g->n;
-      if ((st = dalloc_t(&tl, n + 1, s)) != PB_OK || (st = dalloc_t(&tm, n + 1, s)) != PB_OK ||
-          (st = dalloc_t(&th, n + 1, s)) != PB_OK) break;
+      TierStats ts;
+      if ((st = tier_stats(g, a.rev, 0, n, plan.light_max, plan.med_max, plan.large_max, s, &ts)) != PB_OK) break;
+      if (!g->has_plan) plan_from_stats(g, ts, budget, &plan);
+      // a batch runs one kernel per tier over every graph: hub clusters are
+      // not used, a graph's heavy owners take the dense or the hashed path
+      const bool hashed = plan.agg == PB_AGG_HASH;
+      b->agg[i] = hashed ? PB_AGG_HASH : PB_AGG_BATCH;
+      const uint32_t cl = static_cast<uint32_t>(ts.n[0]), cm = static_cast<uint32_t>(ts.n[1]),
+                     cq = static_cast<uint32_t>(ts.n[2]), ch = static_cast<uint32_t>(ts.n[3]);
+      if ((st = dalloc_t(&tl, cl + 1, s)) != PB_OK || (st = dalloc_t(&tm, cm + 1, s)) != PB_OK ||
+          (st = dalloc_t(&tq, cq + 1, s)) != PB_OK || (st = dalloc_t(&th, ch + 1, s)) != PB_OK) break;
       if (cudaMemsetAsync(tacc, 0, sizeof(unsigned long long) * ACC_WORDS, s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, 0, n, LIGHT_MAX, MED_MAX, UINT64_MAX, tl, tm, th,
-                                                        g->bitsN, tacc);
+      const TierCaps caps = {{cl, cm, cq, ch}};
+      k_classify<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, 0, n, plan.light_max, plan.med_max, plan.large_max,
+                                                        UINT64_MAX, tl, tm, tq, th, g->bitsN, tacc, caps);
       count_launch();
-      unsigned long long hc[ACC_WORDS];
-      if (cudaMemcpyAsync(hc, tacc, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "classify readback"); break; }
-      const uint32_t cl = static_cast<uint32_t>(hc[ACC_NLIGHT]), cm = static_cast<uint32_t>(hc[ACC_NMED]),
-                     ch = static_cast<uint32_t>(hc[ACC_NHEAVY]);
       if (cl) { k_tag_items<<<grid_for(cl, 256, 1024), 256, 0, s>>>(tl, cl, i, b->light + b->nl); count_launch(); }
       if (cm) { k_tag_items<<<grid_for(cm, 256, 1024), 256, 0, s>>>(tm, cm, i, b->med + b->nm); count_launch(); }
+      if (cq) { k_tag_items<<<grid_for(cq, 256, 1024), 256, 0, s>>>(tq, cq, i, b->large + b->nq); count_launch(); }
       if (ch) {
+        dfree(tl, s);
+        tl = nullptr;
+        if ((st = dalloc_t(&tl, ch + 1, s)) != PB_OK) break;
         k_keys_low<<<grid_for(ch, 256, 1024), 256, 0, s>>>(th, ch, g->bitsN, tl);
         count_launch();
-        k_tag_items<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, i, b->heavy + b->nh);
+        TierStats &mx = hashed ? hmax : dmax;
+        const uint64_t side = g->nU > g->nV ? g->nU : g->nV;
+        const uint64_t hr = ts.hrange ? ts.hrange : side;
+        if (hr > mx.hrange) mx.hrange = hr;
+        if (ts.hdist > mx.hdist) mx.hdist = ts.hdist;
+        if (hashed) {
+          k_tag_items<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, i, b->heavy_h + b->nhh);
+          b->nhh += ch;
+        } else {
+          k_tag_items<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, i, b->heavy + b->nh);
+          b->nh += ch;
+        }
         count_launch();
-        // distinct bound of this graph's heavy owners
-        if (cudaMemsetAsync(tacc, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-        k_max_wedges_list<<<grid_for(ch, 256, 1024), 256, 0, s>>>(tl, ch, a.wpre, n, g->nU, a.rev, tacc);
-        count_launch();
-        unsigned long long bd[2] = {0, 0};
-        if (cudaMemcpyAsync(bd, tacc, sizeof(bd), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "readback"); break; }
-        if (bd[0] > max_bound) max_bound = bd[0];
-        if (bd[1] > max_room) max_room = bd[1];
       }
-      b->nl += cl; b->nm += cm; b->nh += ch;
-      dfree(tl, s); dfree(tm, s); dfree(th, s);
-      tl = tm = nullptr; th = nullptr;
+      b->nl += cl; b->nm += cm; b->nq += cq;
+      if (cq && plan.large_max > large_max_all) large_max_all = plan.large_max;
+      // the temporary lists are reused by the next graph only after these kernels
+      if (cudaStreamSynchronize(s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "batch classify"); break; }
+      dfree(tl, s); dfree(tm, s); dfree(tq, s); dfree(th, s);
+      tl = tm = tq = nullptr; th = nullptr;
     }
   } while (0);
-  dfree(tl, s); dfree(tm, s); dfree(th, s); dfree(tacc, s);
+  dfree(tl, s); dfree(tm, s); dfree(tq, s); dfree(th, s); dfree(tacc, s);
   if (st != PB_OK) return st;
   PB_TRY(dalloc_t(&b->tab, ng, s));
   PB_CUDA(cudaMemcpyAsync(b->tab, host_tab.data(), sizeof(CArgs) * ng, cudaMemcpyHostToDevice, s));
+  const uint64_t resident = heavy1_resident(b->device, HB_HOT);
+  if (b->nq) {
+    large_slot_shape(large_max_all, &b->hsm);
+    const size_t smem = hot_words(MH_HOT, true) * sizeof(uint32_t);
+    PB_CUDA(cudaFuncSetAttribute(k_large<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large<true, false, true>, MH_THREADS, smem);
+    uint64_t ns = static_cast<uint64_t>(sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
+    if (ns > b->nq) ns = b->nq;
+    b->nslots_m = ns;
+    PB_TRY(dalloc(&b->scratch_m, ns * large_slot_bytes(b->hsm) + 64, s));
+    b->hsm.hkey = static_cast<uint32_t *>(b->scratch_m);
+    b->hsm.hval = b->hsm.hkey + ns * b->hsm.hcap;
+    b->hsm.T = b->hsm.hval + ns * b->hsm.hcap;
+  }
   if (b->nh) {
-    b->hs.side = max_room < max_side ? max_room : max_side;  // dense histograms span the owners' label ranges
-    b->hs.tcap = max_bound < max_side ? max_bound : max_side;
+    b->hs.side = dmax.hrange < max_side ? dmax.hrange : max_side;  // dense histograms span the owners' label ranges
+    b->hs.tcap = dmax.hdist < b->hs.side ? dmax.hdist : b->hs.side;
     b->slot_bytes = (b->hs.side + b->hs.tcap) * sizeof(uint32_t);
     b->hs.hot = HB_HOT;
-    const size_t hsmem = HB_HOT * sizeof(uint32_t);
-    PB_CUDA(cudaFuncSetAttribute(k_heavy1<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
-    PB_CUDA(cudaFuncSetAttribute(k_heavy1<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<true, false, true>, HB_THREADS, hsmem);
-    uint64_t ns = static_cast<uint64_t>(sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
+    uint64_t ns = resident;
     uint64_t fit = budget / (b->slot_bytes + 32);
     if (fit == 0) return fail(PB_ERR_SCRATCH, "batch scratch budget below one slot");
     if (ns > fit) ns = fit;
@@ -2165,6 +2722,27 @@ static pb_status batch_build(pb_batch *b, uint64_t budget, cudaStream_t s) {
     b->hs.tcnt = b->hs.T + ns * b->hs.tcap;
     b->hs.item = b->hs.tcnt + 2 * ns;
   }
+  if (b->nhh) {
+    b->hsh.tcap = hmax.hdist < max_side ? hmax.hdist : max_side;
+    uint64_t cap = 32;
+    while (cap < 2 * b->hsh.tcap) cap <<= 1;
+    b->hsh.hcap = cap;
+    b->slot_bytes_h = (2 * cap + b->hsh.tcap) * sizeof(uint32_t);
+    b->hsh.hot = HB_HOT;
+    uint64_t ns = resident;
+    uint64_t fit = budget / (b->slot_bytes_h + 32);
+    if (fit == 0) return fail(PB_ERR_SCRATCH, "batch scratch budget below one hashed slot");
+    if (ns > fit) ns = fit;
+    if (ns > b->nhh) ns = b->nhh;
+    b->nslots_h = ns;
+    PB_TRY(dalloc(&b->scratch_h, ns * b->slot_bytes_h + ns * 7 * sizeof(uint32_t) + 64, s));
+    uint32_t *sp = static_cast<uint32_t *>(b->scratch_h);
+    b->hsh.hkey = sp;
+    b->hsh.hval = sp + ns * cap;
+    b->hsh.T = b->hsh.hval + ns * cap;
+    b->hsh.tcnt = b->hsh.T + ns * b->hsh.tcap;
+    b->hsh.item = b->hsh.tcnt + 2 * ns;
+  }
   PB_CUDA(cudaStreamSynchronize(s));
   return b->pv ? batch_capture<true>(b) : batch_capture<false>(b);
 }
@@ -2175,12 +2753,110 @@ using namespace pb;
 
 extern "C" {
 
-pb_status pb_autotune(const pb_graph *g, pb_plan_t *plan) {
+pb_status pb_autotune(const pb_graph *cg, uint64_t scratch_bytes, pb_plan_t *plan) {
   clear_error();
-  if (!g || !plan) return fail(PB_ERR_INVALID, "graph or plan is NULL");
-  PB_TRY(ensure_ranked(g, nullptr));
-  PB_CUDA(cudaStreamSynchronize(nullptr));
-  make_plan(g, plan);
+  if (!cg || !plan) return fail(PB_ERR_INVALID, "graph or plan is NULL");
+  pb_graph *g = const_cast<pb_graph *>(cg);  // planning reads the graph; only its statistics buffer is written
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != g->device) cudaSetDevice(g->device);
+  pb_status st = ensure_ranked(g, nullptr);
+  if (st == PB_OK) st = make_plan(g, scratch_bytes ? scratch_bytes : (uint64_t(16) << 30), nullptr, plan);
+  if (st == PB_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = fail(PB_ERR_CUDA, "autotune");
+  if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
+  return st;
+}
+
+pb_status pb_count_bytes(pb_graph *g, pb_agg agg, uint64_t scratch_bytes, int want_vertex, int want_edge,
+                         int out_on_device, uint64_t *bytes) {
+  clear_error();
+  if (!g || !bytes) return fail(PB_ERR_INVALID, "graph or bytes is NULL");
+  if (agg < PB_AGG_SORT || agg > PB_AGG_AUTO) return fail(PB_ERR_INVALID, "unknown aggregation %d", (int)agg);
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != g->device) cudaSetDevice(g->device);
+  const uint64_t budget = scratch_bytes ? scratch_bytes : (uint64_t(16) << 30);
+  const uint64_t n = g->n, m = g->m, na = 2 * m;
+  constexpr uint64_t SLACK = uint64_t(2) << 20;  // per allocation: the pool's rounding
+  uint64_t b = 0, allocs = 0;
+  auto add = [&](uint64_t x) { b += x; allocs++; };
+  pb_status st = ensure_ranked(g, nullptr);
+  do {
+    if (st != PB_OK) break;
+    add(2 * TS_WORDS * 8);                       // counters and statistics
+    if (want_vertex) add((n + 1) * 8);            // per-vertex accumulators
+    if (want_edge) { add((na + 1) * 8); add((na + 1) * 4); add((m + 1) * 8); }  // per-slot, canonical edges
+    if (!out_on_device && (want_vertex || want_edge))
+      add(((want_vertex ? n : 0) + (want_edge ? g->m_in : 0) + 1) * 8);           // download staging
+    if (g->W == 0) break;
+    if (agg == PB_AGG_SORT) {
+      add(budget);                               // the wedge chunk never exceeds the budget
+      break;
+    }
+    pb_plan_t plan;
+    if (g->has_plan) plan = g->plan;
+    else make_plan_basic(g, &plan);
+    const int rev = g->retrieval == PB_RETRIEVE_AUTO ? plan.retrieval == PB_RETRIEVE_HIGH
+                                                      : g->retrieval == PB_RETRIEVE_HIGH;
+    TierStats ts;
+    unsigned long long *buf = nullptr;
+    if ((st = dalloc_t(&buf, TS_WORDS, nullptr)) != PB_OK) break;
+    st = tier_stats(g, rev, 0, n, plan.light_max, plan.med_max, plan.large_max, nullptr, &ts, buf);
+    dfree(buf, nullptr);
+    if (st != PB_OK) break;
+    if (!g->has_plan) plan_from_stats(g, ts, budget, &plan);
+    const uint64_t nl = ts.n[0], nm = ts.n[1], nq = ts.n[2], nh = ts.n[3];
+    add((nl + 1) * 4); add((nm + 1) * 4); add((nq + 1) * 4); add((nh + 1) * 8);   // tier lists
+    if (nq) {                                                   // large-tier slots (grow only)
+      HeavySlots hm = {};
+      large_slot_shape(plan.large_max, &hm);
+      const uint64_t sc = static_cast<uint64_t>(sm_count(g->device)) * 8 * large_slot_bytes(hm);
+      add(sc > g->scratch2_cap ? sc : 0);
+    }
+    if (nh) {
+      add(nh * 4);                                              // heavy list
+      const uint64_t tiles = (nh + 4095) / 4096;
+      add(nh * 8); add(tiles * 256 * 4); add(tiles * 256 * 4 + 4); add(64 << 10);  // its radix sort
+      const int heavy = agg == PB_AGG_AUTO ? plan.agg : agg;
+      const uint64_t slot = heavy == PB_AGG_HASH ? hash_slot_bytes(g, ts, nullptr, nullptr)
+                                                 : dense_slot_bytes(g, ts, nullptr, nullptr);
+      uint64_t fit = budget / (slot + 16);
+      const uint64_t resident = heavy1_resident(g->device, HOT_SMALL);
+      uint64_t ns = fit < resident ? fit : resident;
+      if (ns < 1) ns = 1;
+      const uint64_t sc = ns * slot + ns * 12 + 64;
+      add(sc > g->scratch_cap ? sc : 0);                        // scratch grows only
+    }
+  } while (0);
+  if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
+  if (st != PB_OK) return st;
+  *bytes = b + allocs * SLACK;
+  return PB_OK;
+}
+
+pb_status pb_set_plan(pb_graph *g, const pb_plan_t *plan) {
+  clear_error();
+  if (!g) return fail(PB_ERR_INVALID, "graph is NULL");
+  if (!plan) {
+    g->has_plan = false;
+    return PB_OK;
+  }
+  if (plan->agg != PB_AGG_BATCH && plan->agg != PB_AGG_HASH && plan->agg != PB_AGG_HIST)
+    return fail(PB_ERR_INVALID, "plan aggregation must be BATCH, HASH or HIST (got %d)", plan->agg);
+  if (plan->retrieval != PB_RETRIEVE_LOW && plan->retrieval != PB_RETRIEVE_HIGH)
+    return fail(PB_ERR_INVALID, "plan retrieval must be LOW or HIGH (got %d)", plan->retrieval);
+  if (plan->hub_cluster < 1 || plan->hub_cluster > 16)
+    return fail(PB_ERR_INVALID, "plan hub_cluster must be in [1, 16] (got %u)", plan->hub_cluster);
+  pb_plan_t p = *plan;
+  if (p.light_max < 1) p.light_max = 1;
+  if (p.light_max > LIGHT_MAX) p.light_max = LIGHT_MAX;
+  if (p.med_max < p.light_max) p.med_max = p.light_max;
+  if (p.med_max > MED_MAX) p.med_max = MED_MAX;
+  if (p.large_max < p.med_max) p.large_max = p.med_max;
+  if (p.large_max > LARGE_LIMIT) p.large_max = LARGE_LIMIT;
+  if (p.hot > HOT_LARGE) p.hot = HOT_LARGE;
+  g->plan = p;
+  g->has_plan = true;
   return PB_OK;
 }
 
@@ -2222,7 +2898,7 @@ pb_status pb_batch_run(pb_batch *b, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PhaseScope ph(PB_PHASE_HEAVY, s);
   PB_CUDA(cudaGraphLaunch(b->exec, s));
-  count_launch((b->nl ? 1 : 0) + (b->nm ? 1 : 0) + (b->nh ? 1 : 0));
+  count_launch((b->nl ? 1 : 0) + (b->nm ? 1 : 0) + (b->nq ? 1 : 0) + (b->nh ? 1 : 0) + (b->nhh ? 1 : 0));
   ph.finish(s, b->W);
   PB_CUDA(cudaStreamSynchronize(s));
   prof_flush();

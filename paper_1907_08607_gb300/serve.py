@@ -9,9 +9,13 @@ worker's own CUDA stream, so work of different requests overlaps on the GPU;
 requests that cannot be admitted yet wait in arrival order, but a later
 request that fits may go first (no head-of-line blocking).
 
-The predicted memory of a request is what the library will allocate for it:
-its outputs (8 B per vertex for per-vertex counts, 8 B per slot for per-edge
-counts) plus the heavy-tier scratch, bounded by the library's default budget.
+The predicted memory of a request is the library's own bound on what the count
+will allocate (pb_count_bytes: outputs, tier lists, heavy-tier scratch under
+the plan the autotuner picks, download staging), computed once per graph and
+kind.  When a worker starts a request it gives the count a share of the
+device's resident blocks equal to one over the requests then in flight
+(pb_set_grid_share), so that concurrent counts run side by side on the SMs
+instead of queueing behind persistent kernels that hold all of them.
 """
 from __future__ import annotations
 
@@ -39,20 +43,13 @@ class Request:
     result: object = None
     wedges: int = 0
     mem: int = 0
+    error: str | None = None
 
 
-def predicted_bytes(G: Graph, kind: str, resident_blocks: int = 304) -> int:
-    """Device bytes a count of this kind is predicted to allocate."""
-    inf = G.info()
-    n = inf.nU + inf.nV
-    side = max(inf.nU, inf.nV)
-    out = 0
-    if kind in ("vertex", "edge"):
-        out += 16 * n                              # per-vertex accumulators + output staging
-    if kind == "edge":
-        out += 16 * inf.m + 8 * inf.m_in           # per-slot accumulators + output staging
-    heavy = min(16 << 30, resident_blocks * 8 * side) if inf.max_wedges_x1 > 4096 else 0
-    return out + heavy + 64 * n                    # tier lists and sort keys
+def predicted_bytes(G, kind: str, agg: str = "auto") -> int:
+    """Device bytes a count of this kind (outputs downloaded to the host) is
+    bounded to allocate, from the library (pb_count_bytes)."""
+    return G.count_bytes(agg, vertex=kind == "vertex", edge=kind == "edge", on_device=False)
 
 
 class Server:
@@ -73,6 +70,9 @@ class Server:
         self.done: list[Request] = []
         self.closed = False
         self.work = queue.Queue()
+        # predicted device bytes per (graph, kind), computed before any worker
+        # starts: planning reads a graph that a worker may be counting later
+        self._mem = {(g, k): predicted_bytes(G, k, agg) for g, G in enumerate(graphs) for k in KINDS}
         self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(workers)]
         self.sched = threading.Thread(target=self._scheduler, daemon=True)
         for t in self.threads:
@@ -80,8 +80,14 @@ class Server:
         self.sched.start()
 
     # -- client side
+    def _predicted(self, g: int, kind: str) -> int:
+        key = (g, kind)
+        if key not in self._mem:
+            self._mem[key] = predicted_bytes(self.graphs[g], kind, self.agg)
+        return self._mem[key]
+
     def submit(self, req: Request):
-        req.mem = predicted_bytes(self.graphs[req.graph], req.kind)
+        req.mem = self._predicted(req.graph, req.kind)
         if req.mem > self.budget:
             raise ValueError(f"request {req.rid} needs {req.mem} B, above the {self.budget} B budget")
         with self.lock:
@@ -140,18 +146,25 @@ class Server:
             if r is None:
                 return
             G = self.graphs[r.graph]
+            with self.lock:
+                in_flight = self.workers - self.free_workers
+            if hasattr(G, "set_grid_share"):
+                G.set_grid_share(1.0 / max(1, in_flight))
             r.start = time.perf_counter()
-            with torch.cuda.stream(stream):
-                if r.kind == "global":
-                    c = G.count_all(self.agg, vertex=False, edge=False, stream=stream)
-                    r.result = c.global_count
-                elif r.kind == "vertex":
-                    c = G.count_all(self.agg, edge=False, stream=stream)
-                    r.result = (c.global_count, c.per_vertex_U, c.per_vertex_V)
-                else:
-                    c = G.count_all(self.agg, vertex=False, stream=stream)
-                    r.result = (c.global_count, c.per_edge)
-            r.wedges = G.wedges
+            try:
+                with torch.cuda.stream(stream):
+                    if r.kind == "global":
+                        c = G.count_all(self.agg, vertex=False, edge=False, stream=stream)
+                        r.result = c.global_count
+                    elif r.kind == "vertex":
+                        c = G.count_all(self.agg, edge=False, stream=stream)
+                        r.result = (c.global_count, c.per_vertex_U, c.per_vertex_V)
+                    else:
+                        c = G.count_all(self.agg, vertex=False, stream=stream)
+                        r.result = (c.global_count, c.per_edge)
+                r.wedges = G.wedges
+            except Exception as exc:  # the request fails; the server keeps serving
+                r.error = repr(exc)
             r.done = time.perf_counter()
             with self.lock:
                 self.busy_graphs.discard(r.graph)
@@ -177,7 +190,7 @@ def request_stream(n: int, rate: float, n_graphs: int, seed: int = 0x5E12):
     return reqs, gaps
 
 
-def replay(server_or_none, graphs, reqs, times, agg="auto"):
+def replay(server_or_none, graphs, reqs, times, agg="auto", timeout: float = 600.0):
     """Feed requests at their arrival times; with server None, process them
     one at a time in arrival order (the plain sequential path)."""
     t0 = time.perf_counter()
@@ -207,7 +220,7 @@ def replay(server_or_none, graphs, reqs, times, agg="auto"):
         if now < t:
             time.sleep(t - now)
         server_or_none.submit(r)
-    done = server_or_none.drain(len(reqs))
+    done = server_or_none.drain(len(reqs), timeout=timeout)
     return done, time.perf_counter() - t0
 
 
@@ -220,6 +233,8 @@ def summarize(done, wall):
 
 
 def same_results(a, b) -> bool:
+    if any(r.error for r in list(a) + list(b)):
+        return False
     for x, y in zip(sorted(a, key=lambda r: r.rid), sorted(b, key=lambda r: r.rid)):
         if x.kind == "global":
             if x.result != y.result:

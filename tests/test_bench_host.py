@@ -1,7 +1,6 @@
 """Host-side logic of bench.py and of the binding's error mapping (no GPU)."""
 import json
 import os
-import shutil
 
 import pytest
 
@@ -17,24 +16,30 @@ def bench():
 
 
 def test_traffic_figures_follow_the_kernel_source(bench, tmp_path, monkeypatch):
-    """roofline.traffic comes from the committed capture only while the
-    kernel source is the one that was captured."""
+    """roofline.traffic comes from a committed capture of the same workload
+    (or of its reduced-scale copy) only while the kernel source is the one
+    that was captured."""
+    import hashlib
+    src = tmp_path / "k.cu"
+    src.write_text("// kernel source at capture time\n")
+    cap = {"captures": [{"workload": "cl3s", "scales_to": "cl3", "source_file": "k.cu",
+                         "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+                         "kernels": {"heavy": {"kernel": "k_heavy1", "dram_bytes_per_wedge": 2.5}}}]}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(cap))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("cl3", "heavy", 1000.0) == pytest.approx(2500.0)   # scaled from the small copy
+    assert bench.measured_traffic("cl3s", "heavy", 10.0) == pytest.approx(25.0)
+    assert bench.measured_traffic("cl2", "heavy", 1000.0) is None      # no capture of that workload
+    assert bench.measured_traffic("cl3", "medium", 1000.0) is None     # no capture of that kernel
+    src.write_text(src.read_text() + "// changed\n")                  # the kernel changed since the capture
+    assert bench.measured_traffic("cl3", "heavy", 1000.0) is None
+    # the committed file parses and names existing sources
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         t = json.load(f)
-    for k in ("light", "medium", "heavy"):
-        assert k in t["kernels"] and t["kernels"][k]["dram_bytes_per_wedge"] > 0
-    # a private copy of the layout: same capture, same source
-    (tmp_path / "profiles").mkdir()
-    shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
-    src = tmp_path / t["source_file"]
-    src.parent.mkdir(parents=True)
-    shutil.copy(os.path.join(ROOT, t["source_file"]), src)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    got = bench.measured_traffic("medium", 1000.0)
-    assert got == pytest.approx(1000.0 * t["kernels"]["medium"]["dram_bytes_per_wedge"])
-    assert bench.measured_traffic("sort", 1000.0) is None        # no capture of that kernel
-    src.write_text(src.read_text() + "\n// changed\n")           # the kernel changed since the capture
-    assert bench.measured_traffic("medium", 1000.0) is None
+    for c in t["captures"]:
+        assert os.path.exists(os.path.join(ROOT, c["source_file"]))
+        assert all(k["dram_bytes_per_wedge"] > 0 for k in c["kernels"].values())
 
 
 def test_clock_summary_reads_samples_and_reasons(bench):

@@ -69,5 +69,5 @@ def test_autotune_plan(pb):
     assert p["W_side"] == w_side and p["W_rank"] == G.wedges
     assert abs(p["f_side"] - (w_side - G.wedges) / w_side) < 1e-12
     assert p["rank"] == ("side" if p["f_side"] < 0.1 else "degree")
-    assert p["retrieval"] in ("low", "high")
+    assert p["retrieval"] in ("low", "high") and p["agg"] in ("batch", "hash", "hist")
     G.free()

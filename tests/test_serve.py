@@ -31,10 +31,8 @@ class _FakeGraph:
         self.active = False
         self.wedges = 10
 
-    def info(self):
-        class I:
-            nU, nV, m, m_in, max_wedges_x1 = 100, 100, 1000, 1000, 10
-        return I()
+    def count_bytes(self, agg, vertex=True, edge=True, on_device=False):
+        return 1000 + (800 if vertex else 0) + (8000 if edge else 0)
 
     def count_all(self, agg, vertex=True, edge=True, stream=None):
         assert not self.active, "two calls on one graph at once"
@@ -104,6 +102,26 @@ class _Null:
 
 
 @pytest.mark.gpu
+def test_predicted_bytes_bound_the_pool_high_water_mark():
+    """The library's bound on a count's allocations (used for admission) is at
+    least what the pool's high-water mark rises by during the count, for every
+    kind, on graphs from the serving pool and with device or host outputs."""
+    import paper_1907_08607_gb300 as pb
+    from paper_1907_08607_gb300 import build
+    build.build()
+    graphs = serve.pool(4, m_lo=1e5, m_hi=3e6)
+    for G in graphs:
+        for kind in ("global", "vertex", "edge"):
+            for on_device in (False, True):
+                bound = G.count_bytes("auto", vertex=kind == "vertex", edge=kind == "edge", on_device=on_device)
+                used, _ = pb.device_memory(reset_peak=True)
+                G.count_all("auto", vertex=kind == "vertex", edge=kind == "edge", on_device=on_device)
+                _, peak = pb.device_memory()
+                assert peak - used <= bound, (kind, on_device, peak - used, bound)
+        G.free()
+
+
+@pytest.mark.gpu
 def test_served_results_equal_alone():
     import paper_1907_08607_gb300 as pb
     from paper_1907_08607_gb300 import build
@@ -113,8 +131,9 @@ def test_served_results_equal_alone():
     alone, _ = serve.replay(None, graphs, reqs, times)
     reqs2, _ = serve.request_stream(60, 200.0, len(graphs), seed=77)
     srv = serve.Server(graphs, workers=4)
-    served, _ = serve.replay(srv, graphs, reqs2, [0.0] * len(reqs2))     # all at once: maximal overlap
+    served = serve.replay(srv, graphs, reqs2, [0.0] * len(reqs2), timeout=300)[0]   # all at once: maximal overlap
     srv.close()
+    assert not [r.error for r in served if r.error]
     assert serve.same_results(alone, served)
     for G in graphs:
         G.free()
