@@ -390,13 +390,17 @@ def run_gb300(args):
             step_host()
         barrier()
         torch.cuda.synchronize()
+        pb.profile(enable=True, reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
         e0.record(stream)
         for _ in range(args.steps):
             step_host()
         e1.record(stream)
         torch.cuda.synchronize()
+        host_s = time.perf_counter() - h0
         barrier()
+        eprof = pb.profile(enable=False)
         ems = e0.elapsed_time(e1)
         if dist is not None:
             t = torch.tensor([ems], device=dev, dtype=torch.float64)
@@ -405,7 +409,11 @@ def run_gb300(args):
         e2e = {"value": world * W / (ems / args.steps / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 8 * g.m,
                "d2h_bytes_per_step": 8 * ((g.nU + g.nV if want_v else 0) + (g.m if want_e else 0)) + 8,
-               "ms_per_step": ems / args.steps}
+               "ms_per_step": ems / args.steps,
+               # where the end-to-end step goes: the library's phases (build
+               # includes the upload, output the download) and the host clock
+               "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in eprof.items() if v["records"]},
+               "host_ms_per_step": 1e3 * host_s / args.steps}
 
     # ---- roofline of the dominant kernel (CUDA events inside the library)
     kern = max(["light", "medium", "large", "heavy", "sort"], key=lambda k: prof[k]["ms"])

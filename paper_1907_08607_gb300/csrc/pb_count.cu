@@ -1116,7 +1116,7 @@ __device__ __forceinline__ uint32_t next_unit(uint32_t *s_next, const uint32_t *
 // registers and adds it to the centre once.  Owners come from the work queue
 // acc[QUEUE].
 template <bool PV, bool PE, bool MULTI, bool HCOLD, int NT, bool HOT16, int QUEUE>
-__global__ void __launch_bounds__(NT) k_owner(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
+__global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
                                               HeavySlots h, const uint64_t *__restrict__ items,
                                               const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t hb_hot[];
@@ -1182,32 +1182,42 @@ __global__ void __launch_bounds__(NT) k_owner(CArgs a0, const uint32_t *__restri
       for (;;) {
         uint32_t c, oy, e_lo;
         if (next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo) == NT) break;
-        for (uint32_t e0 = e_lo; e0 < c; e0 += 32) {
-          const bool act = e0 + lane < c;
-          uint32_t tag = 0;
-          bool isnew = false;
-          if (act) {
-            const uint32_t x2 = a.adj[oy + e0 + lane];
-            const uint32_t r = x2 - base;
-            if (r < h.hot) {
-              isnew = hot_inc<HOT16>(hb_hot, r);
-              tag = HCOLD ? r : x2;
-            } else if (HCOLD) {
-              tag = TCOLD | cold_insert(hkey, hval, lg, x2, isnew, err);
-            } else {
-              isnew = atomicAdd(&A[r], 1u) == 0u;
-              tag = x2;
-            }
+        // two adjacency loads per lane in flight before their counts
+        for (uint32_t e0 = e_lo; e0 < c; e0 += 64) {
+          uint32_t x2v[2];
+#pragma unroll
+          for (int q = 0; q < 2; q++) {
+            const uint32_t e = e0 + 32 * q + lane;
+            x2v[q] = e < c ? a.adj[oy + e] : 0u;
           }
-          const uint32_t bm = __ballot_sync(FULL, isnew);
-          if (bm) {
-            uint32_t b0 = 0;
-            if (lane == 0) b0 = atomicAdd(&s_nt, static_cast<uint32_t>(__popc(bm)));
-            b0 = __shfl_sync(FULL, b0, 0);
-            if (isnew) {
-              const uint32_t at = b0 + __popc(bm & lanemask_lt());
-              if (at < h.tcap) T[at] = tag;
-              else atomicOr(err, 16ull);
+#pragma unroll
+          for (int q = 0; q < 2; q++) {
+            const bool act = e0 + 32 * q + lane < c;
+            uint32_t tag = 0;
+            bool isnew = false;
+            if (act) {
+              const uint32_t x2 = x2v[q];
+              const uint32_t r = x2 - base;
+              if (r < h.hot) {
+                isnew = hot_inc<HOT16>(hb_hot, r);
+                tag = HCOLD ? r : x2;
+              } else if (HCOLD) {
+                tag = TCOLD | cold_insert(hkey, hval, lg, x2, isnew, err);
+              } else {
+                isnew = atomicAdd(&A[r], 1u) == 0u;
+                tag = x2;
+              }
+            }
+            const uint32_t bm = __ballot_sync(FULL, isnew);
+            if (bm) {
+              uint32_t b0 = 0;
+              if (lane == 0) b0 = atomicAdd(&s_nt, static_cast<uint32_t>(__popc(bm)));
+              b0 = __shfl_sync(FULL, b0, 0);
+              if (isnew) {
+                const uint32_t at = b0 + __popc(bm & lanemask_lt());
+                if (at < h.tcap) T[at] = tag;
+                else atomicOr(err, 16ull);
+              }
             }
           }
         }
@@ -1270,15 +1280,23 @@ __global__ void __launch_bounds__(NT) k_owner(CArgs a0, const uint32_t *__restri
           if (k == NT) break;
           const bool nar = PE && s_nar[k];
           unsigned long long sum = 0;
-          for (uint32_t e = e_lo + lane; e < c; e += 32) {
-            const uint32_t sl = oy + e, x2 = a.adj[sl], r = x2 - base;
-            uint32_t d;
-            if (r < h.hot) d = hot_get<HOT16>(hb_hot, r);
-            else if (HCOLD) d = cold_get(hkey, hval, lg, x2, err);
-            else d = __ldcg(&A[r]);
-            if (d > 1) {
-              sum += d - 1;
-              if (PE) es_add_wedge(a, sl, d - 1, nar);
+          for (uint32_t e0 = e_lo + lane; e0 < c; e0 += 64) {
+            uint32_t x2v[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+              const uint32_t e = e0 + 32 * q;
+              if (e >= c) break;
+              const uint32_t sl = oy + e, x2 = x2v[q], r = x2 - base;
+              uint32_t d;
+              if (r < h.hot) d = hot_get<HOT16>(hb_hot, r);
+              else if (HCOLD) d = cold_get(hkey, hval, lg, x2, err);
+              else d = __ldcg(&A[r]);
+              if (d > 1) {
+                sum += d - 1;
+                if (PE) es_add_wedge(a, sl, d - 1, nar);
+              }
             }
           }
           sum = warp_sum(sum);

@@ -361,17 +361,32 @@ __global__ void k_labels(const uint32_t *__restrict__ order, const uint32_t *__r
   }
 }
 
+// The two arcs of every canonical edge, keyed (label(src), maxrank -
+// rank(nbr)), and in the same pass deg_x(x) (degp: the neighbours of x ranked
+// above it): each edge adds one to its lower-ranked endpoint, warp-aggregated
+// since edges come grouped by U endpoint.
 __global__ void k_arc_keys(const uint32_t *__restrict__ eu, const uint32_t *__restrict__ ev, uint64_t m,
                            uint32_t nU, const uint32_t *__restrict__ rank, const uint32_t *__restrict__ label,
-                           int bitsN, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                           int bitsN, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                           uint32_t *__restrict__ degp) {
   const uint64_t mask = (uint64_t(1) << bitsN) - 1;
-  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t a = eu[e], b = nU + ev[e];
-    keys[2 * e] = (static_cast<uint64_t>(label[a]) << bitsN) | (mask - rank[b]);
-    vals[2 * e] = static_cast<uint32_t>(2 * e);
-    keys[2 * e + 1] = (static_cast<uint64_t>(label[b]) << bitsN) | (mask - rank[a]);
-    vals[2 * e + 1] = static_cast<uint32_t>(2 * e + 1);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t iters = (m + stride - 1) / stride;
+  for (size_t itn = 0; itn < iters; itn++) {  // uniform trip count: the whole warp reaches the match
+    const size_t e = start + itn * stride;
+    uint32_t t = 0xffffffffu;
+    if (e < m) {
+      const uint32_t a = eu[e], b = nU + ev[e];
+      const uint32_t ra = rank[a], rb = rank[b], la = label[a], lb = label[b];
+      keys[2 * e] = (static_cast<uint64_t>(la) << bitsN) | (mask - rb);
+      vals[2 * e] = static_cast<uint32_t>(2 * e);
+      keys[2 * e + 1] = (static_cast<uint64_t>(lb) << bitsN) | (mask - ra);
+      vals[2 * e + 1] = static_cast<uint32_t>(2 * e + 1);
+      t = rb > ra ? la : lb;
+    }
+    const uint32_t peers = __match_any_sync(FULL, t);
+    if (t != 0xffffffffu && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&degp[t], __popc(peers));
   }
 }
 
@@ -388,27 +403,6 @@ __global__ void k_arcs_out(const uint64_t *__restrict__ keys, const uint32_t *__
     adj[s] = rlab[mask - (keys[s] & mask)];
     if (a & 1u) slotB[e] = static_cast<uint32_t>(s);  // arc from v to u
     else slotA[e] = static_cast<uint32_t>(s);
-  }
-}
-
-// degp[x] = deg_x(x): the neighbours of x ranked above it.  One pass over the
-// canonical edges: each edge adds one to its lower-ranked endpoint (labels;
-// warp-aggregated, since edges come grouped by U endpoint).
-__global__ void k_degp_edges(const uint32_t *__restrict__ eu, const uint32_t *__restrict__ ev, uint64_t m,
-                             uint32_t nU, const uint32_t *__restrict__ rank, const uint32_t *__restrict__ label,
-                             uint32_t *__restrict__ degp) {
-  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-  const size_t start = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const size_t iters = (m + stride - 1) / stride;
-  for (size_t itn = 0; itn < iters; itn++) {  // uniform trip count: the whole warp reaches the match
-    const size_t e = start + itn * stride;
-    uint32_t t = 0xffffffffu;
-    if (e < m) {
-      const uint32_t a = eu[e], b = nU + ev[e];
-      t = rank[b] > rank[a] ? label[a] : label[b];
-    }
-    const uint32_t peers = __match_any_sync(FULL, t);
-    if (t != 0xffffffffu && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&degp[t], __popc(peers));
   }
 }
 
@@ -582,10 +576,6 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
     dfree(tmp, s);
     tmp = nullptr;
     if (cudaMemsetAsync(g->degp, 0, (n + 1) * sizeof(uint32_t), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
-    if (m > 0) {
-      k_degp_edges<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, g->rank, g->label, g->degp);
-      count_launch();
-    }
     if ((st = dalloc_t(&wc, 2 * (n + 1), s)) != PB_OK) break;  // both directions
     if (cudaMemsetAsync(wc, 0, 2 * (n + 1) * sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
     unsigned long long *wcr = wc + (n + 1);
@@ -594,7 +584,7 @@ pb_status rank_graph(pb_graph *g, int kind, const uint32_t *rank_of, int on_devi
       if ((st = dalloc_t(&keys, na, s)) != PB_OK) break;
       if ((st = dalloc_t(&vals, na, s)) != PB_OK) break;
       k_arc_keys<<<grid_for(m, 256, 8192), 256, 0, s>>>(g->eu, g->ev, m, g->nU, g->rank, g->label, bitsN, keys,
-                                                         vals);
+                                                         vals, g->degp);
       count_launch();
       if ((st = radix_sort(keys, vals, na, 2 * bitsN, s)) != PB_OK) break;
       k_arcs_out<<<grid_for(na, 256, 8192), 256, 0, s>>>(keys, vals, na, bitsN, rlab, g->adj, g->slotA, g->slotB);
