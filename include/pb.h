@@ -268,15 +268,19 @@ pb_status pb_count_approx(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *
  *    with at most light_max wedges (<= 768) are counted one warp each in a
  *    shared-memory hash table; those up to med_max (<= 4096) one 512-thread
  *    block each in a shared-memory hash table; those up to large_max
- *    (<= 65535; the autotuner sets large_max = med_max, which leaves this
- *    tier empty, as the heavy kernel's split work units count such owners at
- *    least as fast) one 256-thread block each, with 16-bit counts of the
- *    first 16384 labels of a side in shared memory and the rest in a small
- *    hash table in device memory; the rest ("heavy") one 1024-thread block each
+ *    (<= 65535) one 256-thread block each, with 16-bit counts of the first
+ *    16384 labels of a side in shared memory and the rest in a small hash
+ *    table in device memory; the rest ("heavy") one 1024-thread block each
  *    with the counts of the first `hot` labels of a side in shared memory and
  *    the rest in device-memory scratch.  hot is the size whose share of
  *    wedge endpoints (hot_hit) pays for its shared memory: 16384 labels, or
  *    49152 when the smaller range catches under 90 % of the endpoints.
+ *    The autotuner sets light_max = 768 and large_max = 4096; med_max is
+ *    4096 (the hash tier takes the mid-size owners) unless their mean wedges
+ *    per neighbour (mid_segment, over the owners of more than light_max and at
+ *    most 65535 wedges) is at least 80, when med_max = light_max and the
+ *    hot-range tier takes them: a warp then walks whole segments instead of
+ *    locating every wedge.
  *  agg (used by PB_AGG_AUTO), from the heavy owners' scratch per slot against
  *    the budget and the device's resident blocks:
  *    BATCH when one dense histogram per resident block fits the budget;
@@ -311,7 +315,7 @@ typedef struct {
   uint64_t slot_bytes_dense;  /* ... with a dense histogram (BATCH, HIST) */
   uint64_t slot_bytes_hash;   /* ... with a hashed cold part (HASH) */
   uint32_t resident_blocks;   /* resident blocks of the heavy kernel */
-  double mid_segment;         /* wedges per neighbour of the owners between med_max and 65535 wedges */
+  double mid_segment;         /* wedges per neighbour of the owners above light_max, up to 65535 wedges */
   uint64_t scratch_bytes;     /* the budget the plan was made for */
 } pb_plan_t;
 pb_status pb_autotune(const pb_graph *g, uint64_t scratch_bytes, pb_plan_t *plan);

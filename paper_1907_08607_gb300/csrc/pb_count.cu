@@ -1060,6 +1060,9 @@ __host__ __device__ constexpr uint32_t hot_words(uint32_t hot, bool hot16) { ret
 // spreads them over all its warps.  The chunk size is the owner's wedges per
 // warp, rounded up to a power of two, at least SEG_CHUNK.
 constexpr uint32_t SEG_CHUNK = 256;
+// Adjacency loads per lane in flight in a segment walk (20M x 60M heavy tier:
+// 823 ms with one, 668 with two, 623 with four).
+constexpr int OWNER_ILP = 4;
 
 // Chunk j of the staged neighbours: the neighbour k it belongs to (first k
 // with ck[k] > j), the end c of the chunk's range in that segment (its
@@ -1182,16 +1185,16 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
       for (;;) {
         uint32_t c, oy, e_lo;
         if (next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo) == NT) break;
-        // two adjacency loads per lane in flight before their counts
-        for (uint32_t e0 = e_lo; e0 < c; e0 += 64) {
-          uint32_t x2v[2];
+        // OWNER_ILP adjacency loads per lane in flight before their counts
+        for (uint32_t e0 = e_lo; e0 < c; e0 += 32 * OWNER_ILP) {
+          uint32_t x2v[OWNER_ILP];
 #pragma unroll
-          for (int q = 0; q < 2; q++) {
+          for (int q = 0; q < OWNER_ILP; q++) {
             const uint32_t e = e0 + 32 * q + lane;
             x2v[q] = e < c ? a.adj[oy + e] : 0u;
           }
 #pragma unroll
-          for (int q = 0; q < 2; q++) {
+          for (int q = 0; q < OWNER_ILP; q++) {
             const bool act = e0 + 32 * q + lane < c;
             uint32_t tag = 0;
             bool isnew = false;
@@ -1280,12 +1283,12 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
           if (k == NT) break;
           const bool nar = PE && s_nar[k];
           unsigned long long sum = 0;
-          for (uint32_t e0 = e_lo + lane; e0 < c; e0 += 64) {
-            uint32_t x2v[2];
+          for (uint32_t e0 = e_lo + lane; e0 < c; e0 += 32 * OWNER_ILP) {
+            uint32_t x2v[OWNER_ILP];
 #pragma unroll
-            for (int q = 0; q < 2; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+            for (int q = 0; q < OWNER_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
+            for (int q = 0; q < OWNER_ILP; q++) {
               const uint32_t e = e0 + 32 * q;
               if (e >= c) break;
               const uint32_t sl = oy + e, x2 = x2v[q], r = x2 - base;
@@ -1345,6 +1348,13 @@ constexpr uint32_t LARGE_LIMIT = 0xffff;  // the large tier's 16-bit counts boun
 // 256-thread one (20M x 60M: 1420 vs 1425 ms per count) or faster (1M x 4M:
 // 47.8 vs 54.3 ms), on every graph measured.  Pinned plans can still use it.
 constexpr uint32_t LARGE_MAX = MED_MAX;
+// Mean wedges per neighbour of the mid-size owners from which the hot-range
+// tier counts them faster than the shared-memory hash tier.  Measured (mid-size
+// tier ms, per-edge counts, hash / hot range): Chung-Lu 2M x 2M gamma 2.5,
+// 9.5 wedges per neighbour: 3.05 / 4.78; 1M x 4M quarter copy, 30: 2.58 / 3.08;
+// 1M x 4M, 42: 14.2 / 18.0; 100k x 300k gamma 2.0, 51: 1.05 / 1.65; 20M x 60M
+// 1/16 copy, 105: 9.26 / 7.47; 20M x 60M, 399: 492.6 / 420.5.
+constexpr double MID_SEGMENT = 80.0;
 constexpr uint32_t MH_HOT = 16384;        // large tier: labels counted in shared memory (16-bit)
 template <bool PV, bool PE, bool MULTI>
 constexpr auto k_large = k_owner<PV, PE, MULTI, true, MH_THREADS, true, ACC_QLARGE>;
@@ -1725,9 +1735,10 @@ __global__ void k_tier_stats(const uint64_t *__restrict__ wpre, const uint64_t *
     cnt[t]++;
     ws[t] += wc;
     maxw = wc > maxw ? wc : maxw;
-    // neighbours of the owners between med_max and the large tier's limit:
-    // their wedges per neighbour (mean segment length) choose the large tier
-    if (wc > med_max && wc <= LARGE_LIMIT_D) {
+    // neighbours of the owners between light_max and the large tier's limit:
+    // their wedges per neighbour (mean segment length) choose the tier of the
+    // mid-size owners
+    if (wc > light_max && wc <= LARGE_LIMIT_D) {
       span += rev ? off[x + 1] - off[x] : degp[x];
       wmid += wc;
     }
@@ -1869,14 +1880,26 @@ static uint64_t large_slot_bytes(const HeavySlots &hm) { return (2 * hm.hcap + h
 
 // The statistics part of the plan: tiers, hot range, and the aggregation that
 // PB_AGG_AUTO uses (rules documented with pb_plan_t).
-static void plan_from_stats(const pb_graph *g, const TierStats &ts, uint64_t budget, pb_plan_t *plan) {
+static void plan_from_stats(const pb_graph *g, TierStats &ts, uint64_t budget, pb_plan_t *plan) {
+  // Mid-size owners (light_max < wedges <= med_max): the shared-memory hash
+  // tier, or -- when their wedges sit in long segments (mean wedges per
+  // neighbour at least MID_SEGMENT) -- the 256-thread hot-range tier, which
+  // walks a segment with a whole warp instead of locating every wedge.  The
+  // owners and wedges of the medium tier then move to the large one.
+  plan->mid_segment = ts.span_mid ? static_cast<double>(ts.w_mid) / static_cast<double>(ts.span_mid) : 0.0;
+  if (plan->mid_segment >= MID_SEGMENT && plan->med_max > plan->light_max) {
+    if (plan->large_max < plan->med_max) plan->large_max = plan->med_max;
+    plan->med_max = plan->light_max;
+    ts.n[2] += ts.n[1];
+    ts.w[2] += ts.w[1];
+    ts.n[1] = ts.w[1] = 0;
+  }
   for (int t = 0; t < 4; t++) {
     plan->owners[t] = ts.n[t];
     plan->wedges[t] = ts.w[t];
   }
   plan->max_owner_wedges = ts.maxw;
   plan->scratch_bytes = budget;
-  plan->mid_segment = ts.span_mid ? static_cast<double>(ts.w_mid) / static_cast<double>(ts.span_mid) : 0.0;
   const double W = g->W ? static_cast<double>(g->W) : 1.0;
   const double hit16 = static_cast<double>(ts.pre[0] + ts.pre[1]) / W;
   const double hit48 = static_cast<double>(ts.pre[2] + ts.pre[3]) / W;
@@ -2329,7 +2352,11 @@ pb_status count_all(pb_graph *g, int agg, uint64_t scratch_bytes, const CountOut
       p.large_max = plan.large_max;
       TierStats ts;
       PB_TRY(tier_stats(g, a.rev, p.owner_lo, p.owner_hi, p.light_max, p.med_max, p.large_max, s, &ts));
-      if (!g->has_plan) plan_from_stats(g, ts, budget, &plan);
+      if (!g->has_plan) {
+        plan_from_stats(g, ts, budget, &plan);
+        p.med_max = plan.med_max;  // the plan may move the mid-size owners to the large tier
+        p.large_max = plan.large_max;
+      }
       p.hot = plan.hot;
       const int heavy = agg == PB_AGG_AUTO ? plan.agg : agg;
       p.heavy = heavy;

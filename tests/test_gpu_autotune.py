@@ -55,6 +55,15 @@ def test_plan_statistics_match_the_wedge_prefix(pb, skewed):
     assert p["hot_hit"] == pytest.approx(hot / G.wedges, rel=1e-12)
     assert p["agg"] in ("batch", "hash", "hist") and p["light_max"] <= 768 and p["med_max"] <= 4096
     assert p["med_max"] <= p["large_max"] <= 65535
+    # mid-size owners' mean wedges per neighbour (the owner's degree under
+    # high retrieval), and the tier it selects for them
+    G.set_retrieval(p["retrieval"])
+    deg = np.diff(G.layout()["off"].cpu().numpy().view(np.uint32).astype(np.int64))
+    span = deg if p["retrieval"] == "high" else None
+    if span is not None:
+        mid = (wc > p["light_max"]) & (wc <= 65535)
+        assert p["mid_segment"] == pytest.approx(wc[mid].sum() / max(span[mid].sum(), 1), rel=1e-12)
+    assert p["med_max"] == (p["light_max"] if p["mid_segment"] >= 80 else 4096) and p["large_max"] == 4096
     G.free()
 
 
