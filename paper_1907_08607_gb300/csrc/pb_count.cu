@@ -1425,6 +1425,10 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
     __syncthreads();
     const uint32_t x1 = s_item;
     if (x1 >= hi) break;
+    if (a.wpre[x1 + 1] == a.wpre[x1]) {  // no wedges here (or counted in shared memory: k_sort_small)
+      __syncthreads();                    // every thread has read s_item
+      continue;
+    }
     const uint64_t kx = static_cast<uint64_t>(x1 - lo) << bitsN;
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     uint64_t *out = EMIT ? keys + (a.wpre[x1] - wbase) : nullptr;
@@ -1482,6 +1486,167 @@ __global__ void __launch_bounds__(MB_THREADS) k_sort_walk(CArgs a, uint32_t lo, 
       done += tot;
       __syncthreads();
     }
+  }
+}
+
+// Sort aggregation for first endpoints with at most SS_MAX wedges: the
+// owner's second endpoints are gathered into shared memory and sorted there
+// (a bitonic network over the next power of two); a run of equal keys is one
+// group, of size d (its last position finds its first by binary search).  The
+// second pass finds each wedge's d by binary search in the sorted keys.
+constexpr int SS_THREADS = 512;
+constexpr uint32_t SS_MAX = 4096;
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *k, uint32_t lo, uint32_t hi, uint32_t key) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (k[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t *k, uint32_t lo, uint32_t hi, uint32_t key) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (k[mid] <= key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <bool PV, bool PE>
+__global__ void __launch_bounds__(SS_THREADS) k_sort_small(CArgs a, uint32_t lo, uint32_t hi) {
+  __shared__ uint32_t K[SS_MAX];
+  __shared__ uint32_t s_incl[SS_THREADS], s_ex[SS_THREADS], s_oy[SS_THREADS];
+  __shared__ unsigned long long s_sum[SS_THREADS];
+  __shared__ uint32_t s_w[33];
+  __shared__ unsigned long long s_w64[33];
+  __shared__ uint32_t s_item;
+  const uint32_t tid = threadIdx.x;
+  unsigned long long gacc = 0;
+  if (PV || PE) s_sum[tid] = 0;
+  for (;;) {
+    if (tid == 0) s_item = lo + static_cast<uint32_t>(atomicAdd(&a.acc[ACC_QLARGE], 1ull));
+    __syncthreads();
+    const uint32_t x1 = s_item;
+    if (x1 >= hi) break;
+    const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
+    if (wc == 0 || wc > SS_MAX) {  // no wedges, or sorted in device memory (k_sort_walk)
+      __syncthreads();             // every thread has read s_item
+      continue;
+    }
+    const uint32_t n_w = static_cast<uint32_t>(wc);
+    const uint32_t base = a.off[x1], dp = owner_span(a, x1);
+    // ---- gather the owner's second endpoints
+    uint32_t done = 0;
+    for (uint32_t k0 = 0; k0 < dp; k0 += SS_THREADS) {
+      const uint32_t i = k0 + tid;
+      uint32_t y, c, oy;
+      owner_nbr(a, base, i, i < dp, y, c, oy);
+      uint32_t tot;
+      const uint32_t incl = block_incl_scan(c, s_w, &tot);
+      s_incl[tid] = incl;
+      s_ex[tid] = incl - c;
+      s_oy[tid] = oy;
+      __syncthreads();
+      for (uint32_t wi = tid; wi < tot; wi += SS_THREADS) {
+        const uint32_t src = block_find(s_incl, SS_THREADS, wi);
+        const uint32_t at = done + wi;
+        if (at < SS_MAX) K[at] = a.adj[s_oy[src] + (wi - s_ex[src])];
+      }
+      done += tot;
+      __syncthreads();
+    }
+    if (done != n_w) {  // the wedge split and the adjacency disagree: record, skip
+      if (tid == 0) atomicOr(&a.acc[ACC_ERR], 32ull);
+      __syncthreads();
+      continue;
+    }
+    uint32_t P = 2;
+    while (P < n_w) P <<= 1;
+    for (uint32_t t = n_w + tid; t < P; t += SS_THREADS) K[t] = 0xffffffffu;
+    __syncthreads();
+    // ---- bitonic sort of K[0, P)
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t t = tid; t < P / 2; t += SS_THREADS) {
+          const uint32_t i = (t / j) * 2 * j + (t % j), l = i + j;
+          const uint32_t ki = K[i], kl = K[l];
+          if ((ki > kl) == ((i & k) == 0)) {
+            K[i] = kl;
+            K[l] = ki;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // ---- groups: C(d, 2) to the global count and both endpoints
+    unsigned long long own = 0;
+    for (uint32_t t = tid; t < n_w; t += SS_THREADS) {
+      const uint32_t key = K[t];
+      if (t + 1 == n_w || K[t + 1] != key) {
+        const unsigned long long d = t + 1 - lower_bound_u32(K, 0, t, key), b = d * (d - 1) / 2;
+        own += b;
+        if (PV && b) atomicAdd(&a.pv[key], b);
+      }
+    }
+    own = block_sum(own, s_w64);
+    if (tid == 0) {
+      gacc += own;
+      if (PV && own) atomicAdd(&a.pv[x1], own);
+    }
+    // ---- centres and edges: d - 1 per wedge
+    if (PV || PE) {
+      for (uint32_t k0 = 0; k0 < dp; k0 += SS_THREADS) {
+        const uint32_t i = k0 + tid;
+        const bool v = i < dp;
+        uint32_t y, c, oy;
+        owner_nbr(a, base, i, v, y, c, oy);
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(c, s_w, &tot);
+        s_incl[tid] = incl;
+        s_ex[tid] = incl - c;
+        s_oy[tid] = oy;
+        __syncthreads();
+        for (uint32_t wb = 0; wb < tot; wb += SS_THREADS) {  // block-uniform trip count
+          const uint32_t wi = wb + tid;
+          uint32_t src = 0;
+          unsigned long long t = 0;
+          if (wi < tot) {
+            src = block_find(s_incl, SS_THREADS, wi);
+            const uint32_t slot = s_oy[src] + (wi - s_ex[src]), x2 = a.adj[slot];
+            const uint32_t lb = lower_bound_u32(K, 0, n_w, x2);
+            const uint32_t d = upper_bound_u32(K, lb, n_w, x2) - lb;
+            if (d > 1) {
+              t = d - 1;
+              if (PE) atomicAdd(&a.es[slot], t);
+            }
+          }
+          warp_run_add(s_sum, src, t);
+        }
+        __syncthreads();
+        if (v) {
+          const unsigned long long sm = s_sum[tid];
+          if (sm) {
+            if (PV) atomicAdd(&a.pv[y], sm);
+            if (PE) atomicAdd(&a.es[base + i], sm);
+            s_sum[tid] = 0;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (tid == 0 && gacc) add_global(a.acc, gacc);
+}
+
+// wl[x] = the wedges of owner x when they are too many for k_sort_small, else 0.
+__global__ void k_wedges_large(const uint64_t *__restrict__ wpre, uint64_t n, uint64_t *__restrict__ wl) {
+  for (size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+       x += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const uint64_t w = wpre[x + 1] - wpre[x];
+    wl[x] = w > SS_MAX ? w : 0;
   }
 }
 
@@ -2176,8 +2341,8 @@ static pb_status reaggregate(uint64_t *keys, unsigned long long *vals, uint64_t 
 }
 
 template <bool PV, bool PE, bool RE>
-static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t olo, uint64_t ohi,
-                          cudaStream_t s) {
+static pb_status run_sort_global(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t olo, uint64_t ohi,
+                                 cudaStream_t s) {
   const uint64_t n = g->n;
   const int bitsN = g->bitsN;
   // bytes per wedge: key, radix ping-pong key, head, run id, run key, run start, run d
@@ -2281,6 +2446,41 @@ static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t
   dfree(dchunk, s); dfree(keys, s); dfree(head, s); dfree(cid, s); dfree(ukey, s); dfree(rstart, s);
   dfree(ud, s); dfree(seg, s);
   dfree(sk.vcnt, s); dfree(sk.vkey, s); dfree(sk.vval, s); dfree(sk.ekey, s); dfree(sk.eval, s);
+  return st;
+}
+
+// Sort aggregation: owners of at most SS_MAX wedges sort in shared memory
+// (k_sort_small); the rest materialise their wedge keys chunk by chunk under
+// the budget and sort them in device memory (run_sort_global), over a wedge
+// prefix that counts only those owners.  Re-aggregation keeps every owner on
+// the device-wide path (its contributions go through the sorted sinks).
+template <bool PV, bool PE, bool RE>
+static pb_status run_sort(pb_graph *g, const CArgs &a, uint64_t budget, uint64_t olo, uint64_t ohi,
+                          cudaStream_t s) {
+  if (RE) return run_sort_global<PV, PE, RE>(g, a, budget, olo, ohi, s);
+  const uint64_t n = g->n;
+  if (ohi > olo) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_small<PV, PE>, SS_THREADS, 0);
+    uint64_t grid = static_cast<uint64_t>(sm_count(g->device)) * (per_sm > 0 ? per_sm : 1);
+    if (grid > ohi - olo) grid = ohi - olo;
+    PB_CUDA(cudaMemsetAsync(a.acc + ACC_QLARGE, 0, sizeof(unsigned long long), s));
+    PB_LAUNCH((k_sort_small<PV, PE>), static_cast<unsigned>(grid), SS_THREADS, 0, s, a, static_cast<uint32_t>(olo),
+              static_cast<uint32_t>(ohi));
+  }
+  uint64_t *wl = nullptr, *wpl = nullptr;
+  pb_status st = PB_OK;
+  do {
+    if ((st = dalloc_t(&wl, n + 1, s)) != PB_OK || (st = dalloc_t(&wpl, n + 1, s)) != PB_OK) break;
+    k_wedges_large<<<grid_for(n, 256, 8192), 256, 0, s>>>(a.wpre, n, wl);
+    count_launch();
+    if ((st = scan_u64(wl, wpl, n, s)) != PB_OK) break;
+    CArgs al = a;
+    al.wpre = wpl;
+    st = run_sort_global<PV, PE, false>(g, al, budget, olo, ohi, s);
+  } while (0);
+  dfree(wl, s);
+  dfree(wpl, s);
   return st;
 }
 
