@@ -1139,12 +1139,14 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
   unsigned long long gacc = 0;
   if (s_hub) hub_zero(s_hub);
   for (uint32_t t = tid; t < hot_words(h.hot, HOT16); t += NT) hb_hot[t] = 0;
-  if (tid == 0) s_nt = 0;
+  // The next owner is fetched by thread 0 during the previous owner's reset
+  // and published by the barrier that ends it (one barrier between owners).
+  if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
+  __syncthreads();
   for (;;) {
-    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
-    __syncthreads();
     const uint32_t it = s_item;
     if (it >= nlist) break;
+    if (tid == 0) s_nt = 0;  // every thread read the previous count before the last barrier
     uint32_t x1;
     CArgs a;  // this item's graph
     if (MULTI) {
@@ -1160,7 +1162,11 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
     const uint64_t wc = a.wpre[x1 + 1] - a.wpre[x1];
     if (HOT16 && wc > 0xffffu) {  // the tier split guarantees 16-bit counts suffice
       __syncthreads();            // every thread has read s_item
-      if (tid == 0) atomicOr(err, 16ull);
+      if (tid == 0) {
+        atomicOr(err, 16ull);
+        s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
+      }
+      __syncthreads();
       continue;
     }
     const int lg = HCOLD ? table_lg(wc, a.n, a.nU, x1, a.rev) : 0;
@@ -1311,7 +1317,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
         __syncthreads();
       }
     }
-    // ---- reset the slot's used entries
+    // ---- reset the slot's used entries (every thread has passed the first
+    // pass's staging barrier, so all have read s_item: fetch the next owner)
+    if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
     for (uint32_t t = tid; t < nt; t += NT) {
       const uint32_t v = T[t];
       if (HCOLD) {
@@ -1329,7 +1337,6 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
       }
     }
     __syncthreads();
-    if (tid == 0) s_nt = 0;
   }
   if (!MULTI && lane == 0) add_global(a0.acc, gacc);
   __syncthreads();
