@@ -30,6 +30,7 @@
 #include <cstdlib>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "pb_common.cuh"
@@ -85,7 +86,7 @@ constexpr int HB_THREADS = 1024;
 // few centres above the limit keep 64-bit counters.  An edge's count is the
 // sum of both arrays over its two slots.
 __device__ __forceinline__ bool es_narrow(const CArgs &a, uint32_t x1, uint32_t dy) {
-  return dy - 1 <= a.nlim[x1 < a.nU ? 0 : 1];
+  return dy - 1 <= (x1 < a.nU ? a.nlim[0] : a.nlim[1]);  // constant indices keep a copy of CArgs in registers
 }
 
 __device__ __forceinline__ void es_add_wedge(const CArgs &a, uint32_t sl, uint32_t t, bool narrow) {
@@ -1052,6 +1053,38 @@ __device__ __forceinline__ void hot_clear(uint32_t *hot, uint32_t r) {
   else hot[r] = 0;
 }
 __host__ __device__ constexpr uint32_t hot_words(uint32_t hot, bool hot16) { return hot16 ? (hot + 1) / 2 : hot; }
+// Count without the first-occurrence test (owners whose hot range is read
+// whole afterwards).
+template <bool HOT16>
+__device__ __forceinline__ void hot_add(uint32_t *hot, uint32_t r) {
+  if (HOT16) atomicAdd(&hot[r >> 1], 1u << ((r & 1u) << 4));
+  else atomicAdd(&hot[r], 1u);
+}
+
+// Owners with at least hot_words / HOT_SCAN_DIV wedges keep no record of
+// which hot labels they touched: after counting, the block reads the whole hot
+// range (four words per thread and load) for the endpoint sums, and clears it
+// after the centre pass.  Below that the touched list is cheaper than the read
+// (the record costs a vote and a compare per wedge, the read a fixed few
+// instructions per hot word).
+constexpr uint32_t HOT_SCAN_DIV = 4;
+
+// C(d, 2) of the counts in hot word w (one count, or two 16-bit ones), with
+// the per-vertex contribution of each second endpoint base + entry.
+template <bool PV, bool HOT16>
+__device__ __forceinline__ unsigned long long hot_word_sum(uint32_t v, uint32_t w, uint32_t base,
+                                                           unsigned long long *s_hub, const CArgs &a) {
+  if (!v) return 0;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < (HOT16 ? 2 : 1); k++) {
+    const unsigned long long d = HOT16 ? (v >> (16 * k)) & 0xffffu : v;
+    const unsigned long long b = d * (d - 1) / 2;
+    s += b;
+    if (PV && b) pv_add(s_hub, a, base + (HOT16 ? 2 * w + k : w), b);
+  }
+  return s;
+}
 
 // Work unit of the one-block kernels: a neighbour's whole segment of second
 // endpoints, or -- when some staged segment is longer than twice the owner's
@@ -1103,6 +1136,82 @@ __device__ __forceinline__ uint32_t next_unit(uint32_t *s_next, const uint32_t *
   return j;
 }
 
+// Counting walk of one work unit (positions [e_lo, c) of the segment at oy)
+// for owners that read their hot range whole: no first-occurrence record for
+// hot labels, so lanes walk independently; a cold label seen for the first
+// time is appended to the touched list with its own shared-memory add (cold
+// labels are a small share of the wedges).
+template <bool HOT16, bool HCOLD>
+__device__ __forceinline__ void owner_count_scan(const CArgs &a, uint32_t *hb_hot, const HeavySlots &h, uint32_t *A,
+                                                 uint32_t *hkey, uint32_t *hval, uint32_t *T, uint32_t *s_nt, int lg,
+                                                 uint32_t base, uint32_t oy, uint32_t e_lo, uint32_t c,
+                                                 unsigned long long *err) {
+  for (uint32_t e0 = e_lo + lane_id(); e0 < c; e0 += 32 * OWNER_ILP) {
+    uint32_t x2v[OWNER_ILP];
+#pragma unroll
+    for (int q = 0; q < OWNER_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+#pragma unroll
+    for (int q = 0; q < OWNER_ILP; q++) {
+      if (e0 + 32 * q >= c) break;
+      const uint32_t x2 = x2v[q], r = x2 - base;
+      if (r < h.hot) {
+        hot_add<HOT16>(hb_hot, r);
+        continue;
+      }
+      bool isnew;
+      uint32_t tag;
+      if (HCOLD) {
+        tag = TCOLD | cold_insert(hkey, hval, lg, x2, isnew, err);
+      } else {
+        isnew = atomicAdd(&A[r], 1u) == 0u;
+        tag = x2;
+      }
+      if (isnew) {
+        const uint32_t at = atomicAdd(s_nt, 1u);
+        if (at < h.tcap) T[at] = tag;
+        else atomicOr(err, 16ull);
+      }
+    }
+  }
+}
+
+// Centre walk of one work unit: the count d of every wedge's second endpoint,
+// d - 1 added to the wedge's edge slot (32-bit partials when NARROW) and
+// summed for the centre.  Returns this lane's sum.  With 16-bit hot counts
+// every owner has fewer than 2^16 wedges, so a 32-bit sum cannot wrap.
+template <bool PE, bool HOT16, bool HCOLD, bool NARROW>
+__device__ __forceinline__ unsigned long long owner_centre_walk(const CArgs &a, const uint32_t *hb_hot,
+                                                                const HeavySlots &h, const uint32_t *A,
+                                                                const uint32_t *hkey, const uint32_t *hval, int lg,
+                                                                uint32_t base, uint32_t oy, uint32_t e_lo, uint32_t c,
+                                                                unsigned long long *err) {
+  using S = typename std::conditional<HOT16, uint32_t, unsigned long long>::type;
+  S sum = 0;
+  for (uint32_t e0 = e_lo + lane_id(); e0 < c; e0 += 32 * OWNER_ILP) {
+    uint32_t x2v[OWNER_ILP];
+#pragma unroll
+    for (int q = 0; q < OWNER_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+#pragma unroll
+    for (int q = 0; q < OWNER_ILP; q++) {
+      const uint32_t e = e0 + 32 * q;
+      if (e >= c) break;
+      const uint32_t x2 = x2v[q], r = x2 - base;
+      uint32_t d;
+      if (r < h.hot) d = hot_get<HOT16>(hb_hot, r);
+      else if (HCOLD) d = cold_get(hkey, hval, lg, x2, err);
+      else d = __ldcg(&A[r]);
+      if (d > 1) {
+        sum += d - 1;
+        if (PE) {
+          if (NARROW) atomicAdd(&a.es32[oy + e], d - 1);
+          else atomicAdd(&a.es[oy + e], static_cast<unsigned long long>(d - 1));
+        }
+      }
+    }
+  }
+  return warp_sum(sum);
+}
+
 // One block of NT threads per owner and slot: the heavy tier (NT = 1024,
 // 32-bit hot counts, cold part dense or hashed) and the medium tier (NT =
 // 256, 16-bit hot counts, cold part hashed).  The owner's neighbours are
@@ -1118,11 +1227,16 @@ __device__ __forceinline__ uint32_t next_unit(uint32_t *s_next, const uint32_t *
 // the top bit set (hashed).  The second pass sums d - 1 over a segment in
 // registers and adds it to the centre once.  Owners come from the work queue
 // acc[QUEUE].
+// Blocks per SM the launch bound promises: a full SM of 1024-thread blocks;
+// 256-thread blocks are held to six per SM by their 32 KB of hot counts, so
+// they may use the registers of six.
+constexpr int owner_min_blocks(int nt) { return nt >= 1024 ? 2048 / nt : 6; }
+
 template <bool PV, bool PE, bool MULTI, bool HCOLD, int NT, bool HOT16, int QUEUE>
-__global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
+__global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
                                               HeavySlots h, const uint64_t *__restrict__ items,
                                               const CArgs *__restrict__ tab) {
-  extern __shared__ uint32_t hb_hot[];
+  extern __shared__ __align__(16) uint32_t hb_hot[];
   __shared__ uint32_t s_c[NT], s_oy[NT], s_y[NT];
   __shared__ uint32_t s_ck[NT];  // inclusive prefix of the staged neighbours' chunk counts
   __shared__ uint32_t s_w[33];
@@ -1137,8 +1251,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
   uint32_t *T = h.T + static_cast<size_t>(slot) * h.tcap;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
+  const uint32_t hw = hot_words(h.hot, HOT16), hw4 = hw & ~3u;
   if (s_hub) hub_zero(s_hub);
-  for (uint32_t t = tid; t < hot_words(h.hot, HOT16); t += NT) hb_hot[t] = 0;
+  for (uint32_t t = tid; t < hw; t += NT) hb_hot[t] = 0;
   // The next owner is fetched by thread 0 during the previous owner's reset
   // and published by the barrier that ends it (one barrier between owners).
   if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
@@ -1170,6 +1285,8 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
       continue;
     }
     const int lg = HCOLD ? table_lg(wc, a.n, a.nU, x1, a.rev) : 0;
+    // hot labels go unrecorded and the hot range is read whole (block-uniform)
+    const bool scan = wc * HOT_SCAN_DIV >= hw;
     // ---- aggregate
     uint32_t ch = SEG_CHUNK;
     while (static_cast<uint64_t>(ch) * (NT / 32) < wc) ch <<= 1;
@@ -1178,10 +1295,12 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
     for (uint32_t s0 = 0; s0 < dp; s0 += NT) {
       {
         uint32_t y, c, oy;
-        owner_nbr(a, xbase, s0 + tid, s0 + tid < dp, y, c, oy);
+        const bool v = s0 + tid < dp;
+        owner_nbr(a, xbase, s0 + tid, v, y, c, oy);
         s_c[tid] = c;
         s_oy[tid] = oy;
         s_y[tid] = y;
+        if (PE && dp <= NT) s_nar[tid] = v && es_narrow(a, x1, a.off[y + 1] - a.off[y]);
         if (tid == 0) s_next = 0;
         split = __syncthreads_or(c > 2 * ch);
         if (split) s_ck[tid] = block_incl_scan((c + ch - 1) / ch, s_w, &units);  // barriers inside
@@ -1191,6 +1310,10 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
       for (;;) {
         uint32_t c, oy, e_lo;
         if (next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo) == NT) break;
+        if (scan) {
+          owner_count_scan<HOT16, HCOLD>(a, hb_hot, h, A, hkey, hval, T, &s_nt, lg, base, oy, e_lo, c, err);
+          continue;
+        }
         // OWNER_ILP adjacency loads per lane in flight before their counts
         for (uint32_t e0 = e_lo; e0 < c; e0 += 32 * OWNER_ILP) {
           uint32_t x2v[OWNER_ILP];
@@ -1201,6 +1324,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
           }
 #pragma unroll
           for (int q = 0; q < OWNER_ILP; q++) {
+            if (e0 + 32 * q >= c) break;  // warp-uniform
             const bool act = e0 + 32 * q + lane < c;
             uint32_t tag = 0;
             bool isnew = false;
@@ -1236,7 +1360,20 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
     const uint32_t nt = s_nt < h.tcap ? s_nt : static_cast<uint32_t>(h.tcap);
     // ---- endpoints: C(d, 2) per distinct second endpoint
     unsigned long long own = 0;
-    for (uint32_t t = tid; t < nt; t += NT) {
+    if (scan) {  // the hot range whole; with global counts alone it is cleared on the way
+      for (uint32_t w = 4 * tid; w < hw4; w += 4 * NT) {
+        uint4 &q4 = *reinterpret_cast<uint4 *>(&hb_hot[w]);
+        const uint4 v4 = q4;
+        if (!PV && !PE) q4 = make_uint4(0u, 0u, 0u, 0u);
+        own += hot_word_sum<PV, HOT16>(v4.x, w, base, s_hub, a) + hot_word_sum<PV, HOT16>(v4.y, w + 1, base, s_hub, a) +
+               hot_word_sum<PV, HOT16>(v4.z, w + 2, base, s_hub, a) + hot_word_sum<PV, HOT16>(v4.w, w + 3, base, s_hub, a);
+      }
+      for (uint32_t w = hw4 + tid; w < hw; w += NT) {
+        own += hot_word_sum<PV, HOT16>(hb_hot[w], w, base, s_hub, a);
+        if (!PV && !PE) hb_hot[w] = 0;
+      }
+    }
+    for (uint32_t t = tid; t < nt; t += NT) {  // recorded labels (cold ones only when scanning)
       const uint32_t v = T[t];
       uint32_t x2;
       unsigned long long d;
@@ -1267,48 +1404,27 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
     // ---- centres and edges: d - 1 per wedge
     if (PV || PE) {
       for (uint32_t s0 = 0; s0 < dp; s0 += NT) {
-        {
+        if (tid == 0) s_next = 0;
+        if (dp > NT) {  // otherwise the first pass's staging is still in place
           uint32_t y, c, oy;
           const bool v = s0 + tid < dp;
           owner_nbr(a, xbase, s0 + tid, v, y, c, oy);
           if (PE) s_nar[tid] = v && es_narrow(a, x1, a.off[y + 1] - a.off[y]);
-          if (tid == 0) s_next = 0;
-          if (dp > NT) {  // otherwise the first pass's staging is still in place
-            s_c[tid] = c;
-            s_oy[tid] = oy;
-            s_y[tid] = y;
-            split = __syncthreads_or(c > 2 * ch);
-            if (split) s_ck[tid] = block_incl_scan((c + ch - 1) / ch, s_w, &units);  // barriers inside
-            else units = dp - s0 < NT ? dp - s0 : NT;
-          }
+          s_c[tid] = c;
+          s_oy[tid] = oy;
+          s_y[tid] = y;
+          split = __syncthreads_or(c > 2 * ch);
+          if (split) s_ck[tid] = block_incl_scan((c + ch - 1) / ch, s_w, &units);  // barriers inside
+          else units = dp - s0 < NT ? dp - s0 : NT;
         }
         __syncthreads();
         for (;;) {
           uint32_t c, oy, e_lo;
           const uint32_t k = next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo);
           if (k == NT) break;
-          const bool nar = PE && s_nar[k];
-          unsigned long long sum = 0;
-          for (uint32_t e0 = e_lo + lane; e0 < c; e0 += 32 * OWNER_ILP) {
-            uint32_t x2v[OWNER_ILP];
-#pragma unroll
-            for (int q = 0; q < OWNER_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
-#pragma unroll
-            for (int q = 0; q < OWNER_ILP; q++) {
-              const uint32_t e = e0 + 32 * q;
-              if (e >= c) break;
-              const uint32_t sl = oy + e, x2 = x2v[q], r = x2 - base;
-              uint32_t d;
-              if (r < h.hot) d = hot_get<HOT16>(hb_hot, r);
-              else if (HCOLD) d = cold_get(hkey, hval, lg, x2, err);
-              else d = __ldcg(&A[r]);
-              if (d > 1) {
-                sum += d - 1;
-                if (PE) es_add_wedge(a, sl, d - 1, nar);
-              }
-            }
-          }
-          sum = warp_sum(sum);
+          const unsigned long long sum =
+              (PE && s_nar[k]) ? owner_centre_walk<PE, HOT16, HCOLD, true>(a, hb_hot, h, A, hkey, hval, lg, base, oy, e_lo, c, err)
+                               : owner_centre_walk<PE, HOT16, HCOLD, false>(a, hb_hot, h, A, hkey, hval, lg, base, oy, e_lo, c, err);
           if (lane == 0 && sum) {
             if (PV) pv_add(s_hub, a, s_y[k], sum);
             if (PE) atomicAdd(&a.es[xbase + s0 + k], sum);
@@ -1320,6 +1436,10 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_owner(CArgs a0, const uint32_
     // ---- reset the slot's used entries (every thread has passed the first
     // pass's staging barrier, so all have read s_item: fetch the next owner)
     if (tid == 0) s_item = static_cast<uint32_t>(atomicAdd(&a0.acc[QUEUE], 1ull));
+    if (scan && (PV || PE)) {
+      for (uint32_t w = 4 * tid; w < hw4; w += 4 * NT) *reinterpret_cast<uint4 *>(&hb_hot[w]) = make_uint4(0u, 0u, 0u, 0u);
+      for (uint32_t w = hw4 + tid; w < hw; w += NT) hb_hot[w] = 0;
+    }
     for (uint32_t t = tid; t < nt; t += NT) {
       const uint32_t v = T[t];
       if (HCOLD) {
