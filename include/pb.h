@@ -268,11 +268,11 @@ pb_status pb_count_approx(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *
  *    with at most light_max wedges (<= 768) are counted one warp each in a
  *    shared-memory hash table; those up to med_max (<= 4096) one 512-thread
  *    block each in a shared-memory hash table; those up to large_max
- *    (<= 65535) one 256-thread block each, with 16-bit counts of the first
- *    16384 labels of a side in shared memory and the rest in a small hash
- *    table in device memory; the rest ("heavy") one 1024-thread block each
- *    with the counts of the first `hot` labels of a side in shared memory and
- *    the rest in device-memory scratch.  hot is the size whose share of
+ *    (<= 65535) one 256-thread block each (eight per SM), with 16-bit counts
+ *    of the first 8192 labels of a side in shared memory and the rest in a
+ *    small hash table in device memory; the rest ("heavy") one 1024-thread
+ *    block each with the counts of the first `hot` labels of a side in shared
+ *    memory and the rest in device-memory scratch.  hot is the size whose share of
  *    wedge endpoints (hot_hit) pays for its shared memory: 16384 labels, or
  *    49152 when the smaller range catches under 90 % of the endpoints.
  *    The autotuner sets light_max = 768 and large_max = 4096; med_max is

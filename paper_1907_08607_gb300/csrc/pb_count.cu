@@ -1227,10 +1227,18 @@ __device__ __forceinline__ unsigned long long owner_centre_walk(const CArgs &a, 
 // the top bit set (hashed).  The second pass sums d - 1 over a segment in
 // registers and adds it to the centre once.  Owners come from the work queue
 // acc[QUEUE].
-// Blocks per SM the launch bound promises: a full SM of 1024-thread blocks;
-// 256-thread blocks are held to six per SM by their 32 KB of hot counts, so
-// they may use the registers of six.
-constexpr int owner_min_blocks(int nt) { return nt >= 1024 ? 2048 / nt : 6; }
+// Block sizes of the one-block owner kernels: the heavy tier's (32-bit hot
+// counts of the plan's hot range) and the large tier's (16-bit counts of
+// MH_HOT labels).  Owners are latency-bound (a chain of dependent loads to
+// stage the neighbours, block barriers between passes), so the large tier is
+// sized for a full SM: eight 256-thread blocks, whose 16 KB of hot counts fit
+// eight to an SM (20M x 60M large tier: 413 ms with 16,384 labels and six
+// blocks per SM, 324 ms with 8,192 and eight; 128-thread blocks with 8,192
+// labels, 331 ms; 64-thread blocks, 385 ms).
+constexpr int H1_THREADS = HB_THREADS;
+constexpr int MH_THREADS = 256;
+constexpr uint32_t MH_HOT = 8192;  // large tier: labels counted in shared memory (16-bit)
+constexpr int owner_min_blocks(int nt) { return 2048 / nt; }
 
 template <bool PV, bool PE, bool MULTI, bool HCOLD, int NT, bool HOT16, int QUEUE>
 __global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, const uint32_t *__restrict__ list, uint32_t nlist,
@@ -1467,8 +1475,7 @@ __global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, co
 // cold part) and the large tier's (MH_THREADS threads, 16-bit hot counts,
 // hashed cold part).
 template <bool PV, bool PE, bool MULTI, bool HCOLD>
-constexpr auto k_heavy1 = k_owner<PV, PE, MULTI, HCOLD, HB_THREADS, false, ACC_QHEAVY>;
-constexpr int MH_THREADS = 256;
+constexpr auto k_heavy1 = k_owner<PV, PE, MULTI, HCOLD, H1_THREADS, false, ACC_QHEAVY>;
 constexpr uint32_t LARGE_LIMIT = 0xffff;  // the large tier's 16-bit counts bound its owners' wedges
 // The large tier is off by default (large_max = med_max): with work split into
 // chunks, the 1024-thread kernel counts owners of 4K-16K wedges as fast as the
@@ -1482,7 +1489,6 @@ constexpr uint32_t LARGE_MAX = MED_MAX;
 // 1M x 4M, 42: 14.2 / 18.0; 100k x 300k gamma 2.0, 51: 1.05 / 1.65; 20M x 60M
 // 1/16 copy, 105: 9.26 / 7.47; 20M x 60M, 399: 492.6 / 420.5.
 constexpr double MID_SEGMENT = 80.0;
-constexpr uint32_t MH_HOT = 16384;        // large tier: labels counted in shared memory (16-bit)
 template <bool PV, bool PE, bool MULTI>
 constexpr auto k_large = k_owner<PV, PE, MULTI, true, MH_THREADS, true, ACC_QLARGE>;
 
@@ -2153,7 +2159,7 @@ static uint64_t heavy1_resident(int device, uint32_t hot) {
   int per_sm = 0;
   const size_t smem = hot * sizeof(uint32_t);
   cudaFuncSetAttribute(k_heavy1<false, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<false, true, false, false>, HB_THREADS,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy1<false, true, false, false>, H1_THREADS,
                                                     smem) != cudaSuccess)
     cudaGetLastError();
   return static_cast<uint64_t>(sm_count(device)) * (per_sm > 0 ? per_sm : 1);
@@ -2365,7 +2371,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, const Tie
         if (one) {
           PB_CUDA(cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
           int per_sm = 0;
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, HB_THREADS, hsmem);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, H1_THREADS, hsmem);
           nc = sms * (per_sm > 0 ? per_sm : 1);
         } else {
           nc = max_clusters(ckern, HB_THREADS, cl, hsmem);
@@ -2396,7 +2402,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, const Tie
         if (cudaMemsetAsync(hs.tcnt, 0, 3 * nslots * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMemsetAsync(a.acc + ACC_QHEAVY, 0, sizeof(unsigned long long), s) != cudaSuccess) { st = fail(PB_ERR_CUDA, "memset"); break; }
         if (one) {
-          PB_LAUNCH(okern, static_cast<unsigned>(nslots), HB_THREADS, hsmem, s, a, pt.list, pt.cnt, hs,
+          PB_LAUNCH(okern, static_cast<unsigned>(nslots), H1_THREADS, hsmem, s, a, pt.list, pt.cnt, hs,
                     (const uint64_t *)nullptr, (const CArgs *)nullptr);
         } else if ((st = launch_cluster(ckern, static_cast<unsigned>(nslots * cl), HB_THREADS, cl, hsmem, s, a, pt.list,
                                         pt.cnt, hs, (const uint64_t *)nullptr, (const CArgs *)nullptr)) != PB_OK) {
@@ -2925,7 +2931,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
     if (b->nh) {
       e1 = cudaMemsetAsync(b->scratch, 0, b->nslots * b->slot_bytes + b->nslots * 7 * sizeof(uint32_t) + 64, s);
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (slots)", __FILE__, __LINE__); break; }
-      k_heavy1<PV, false, true, false><<<static_cast<unsigned>(b->nslots), HB_THREADS, b->hs.hot * sizeof(uint32_t),
+      k_heavy1<PV, false, true, false><<<static_cast<unsigned>(b->nslots), H1_THREADS, b->hs.hot * sizeof(uint32_t),
                                          s>>>(a0, nullptr, b->nh, b->hs, b->heavy, b->tab);
       count_launch();
       e1 = cudaGetLastError();
@@ -2938,7 +2944,7 @@ static pb_status batch_capture_on(pb_batch *b, cudaStream_t s) {
       if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->hsh.tcnt, 0, 3 * b->nslots_h * sizeof(uint32_t), s);
       if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->bacc + ACC_QHEAVY, 0, sizeof(unsigned long long), s);
       if (e1 != cudaSuccess) { st = cuda_fail(e1, "batch memset (hashed slots)", __FILE__, __LINE__); break; }
-      k_heavy1<PV, false, true, true><<<static_cast<unsigned>(b->nslots_h), HB_THREADS,
+      k_heavy1<PV, false, true, true><<<static_cast<unsigned>(b->nslots_h), H1_THREADS,
                                         b->hsh.hot * sizeof(uint32_t), s>>>(a0, nullptr, b->nhh, b->hsh, b->heavy_h,
                                                                             b->tab);
       count_launch();
