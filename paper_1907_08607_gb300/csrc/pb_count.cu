@@ -363,16 +363,49 @@ __device__ __forceinline__ void warp_run_add_rx(unsigned long long *acc, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Light tier: one warp per owner; per-warp table with 16-bit counts; LW_BATCH
-// steps of 32 wedges in flight per warp.
-constexpr int LW_BATCH = 2;
+// Light tier: one warp per owner, per-warp table with 16-bit counts.  Light
+// owners have few neighbours with long segments (the 1/16 copy of 20M x 60M:
+// two to three non-empty segments of ~95 wedges per owner, 95 % of the light
+// wedges in segments of 32 or more), so the warp walks one segment at a time
+// with its lanes (coalesced adjacency reads, LW_ILP loads per lane in flight)
+// and sums a segment's d - 1 in registers: no per-wedge search for the
+// wedge's neighbour and no per-wedge run reduction.
+constexpr int LW_ILP = 4;
+
+// Centre walk of one segment (positions [0, c) of the list at oy): d - 1 of
+// every wedge added to its edge slot (32-bit partials when NARROW), the sum
+// over the segment returned to every lane.  d <= LIGHT_MAX, so the sum fits
+// 32 bits.
+template <bool PE, bool NARROW>
+__device__ __forceinline__ uint32_t light_centre_walk(const CArgs &a, const uint32_t *key, const uint32_t *cnt,
+                                                      int lg, uint32_t oy, uint32_t c, unsigned long long *err) {
+  uint32_t sum = 0;
+  for (uint32_t e0 = lane_id(); e0 < c; e0 += 32 * LW_ILP) {
+    uint32_t x2v[LW_ILP];
+#pragma unroll
+    for (int q = 0; q < LW_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+#pragma unroll
+    for (int q = 0; q < LW_ILP; q++) {
+      const uint32_t e = e0 + 32 * q;
+      if (e >= c) break;
+      const uint32_t d = sh_get16(key, cnt, lg, x2v[q], err);
+      if (d > 1) {
+        sum += d - 1;
+        if (PE) {
+          if (NARROW) atomicAdd(&a.es32[oy + e], d - 1);
+          else atomicAdd(&a.es[oy + e], static_cast<unsigned long long>(d - 1));
+        }
+      }
+    }
+  }
+  return warp_sum(sum);
+}
 
 template <bool PV, bool PE, bool MULTI>
 __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_t *__restrict__ list,
                                                       uint32_t nlist, const uint64_t *__restrict__ items,
                                                       const CArgs *__restrict__ tab) {
   extern __shared__ uint32_t dsm[];  // per warp: LW_CAP keys, then LW_CAP / 2 count words
-  __shared__ unsigned long long s_sum[LW_WARPS][32];
   __shared__ uint32_t s_occ[LW_WARPS][LW_CAP / 32];  // per warp: occupied table entries
   __shared__ unsigned long long s_hubarr[2 * HUBK];
   unsigned long long *s_hub = (PV && !MULTI) ? s_hubarr : nullptr;
@@ -381,7 +414,6 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
   static_assert(LW_CAP == 32 * 32, "one bitmap word of 32 entries per lane");
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
-  if (PV || PE) s_sum[w][lane] = 0;
   if (s_hub) hub_zero(s_hub);
   // The table always has LW_CAP entries and is cleared once; each owner marks
   // the entries it takes in occ, and its endpoint phase and reset visit only
@@ -405,26 +437,25 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
     const uint32_t base = a.off[x1], dp = owner_span(a, x1);
     // An owner with at most 32 neighbours has one chunk: its neighbour data
     // stay in registers for the second pass.
-    uint32_t ky = 0, kc = 0, koy = 0, kincl = 0;
+    uint32_t ky = 0, kc = 0, koy = 0;
     for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
       const uint32_t i = k0 + lane;
-      const bool v = i < dp;
       uint32_t y, c, oy;
-      owner_nbr(a, base, i, v, y, c, oy);
-      const uint32_t incl = warp_incl_scan(c), tot = __shfl_sync(FULL, incl, 31);
-      ky = y; kc = c; koy = oy; kincl = incl;
-      for (uint32_t wb = 0; wb < tot; wb += LW_BATCH * 32) {
-        uint32_t x2v[LW_BATCH];
+      owner_nbr(a, base, i, i < dp, y, c, oy);
+      ky = y; kc = c; koy = oy;
+      for (uint32_t bm = __ballot_sync(FULL, c > 0); bm; bm &= bm - 1) {
+        const int j = __ffs(bm) - 1;
+        const uint32_t cj = __shfl_sync(FULL, c, j), oyj = __shfl_sync(FULL, oy, j);
+        for (uint32_t e0 = lane; e0 < cj; e0 += 32 * LW_ILP) {
+          uint32_t x2v[LW_ILP];
 #pragma unroll
-        for (int q = 0; q < LW_BATCH; q++) {
-          const uint32_t wi = wb + q * 32 + lane;
-          uint32_t src, slot;
-          warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, src, slot);
-          x2v[q] = wi < tot ? a.adj[slot] : 0;
+          for (int q = 0; q < LW_ILP; q++) x2v[q] = e0 + 32 * q < cj ? a.adj[oyj + e0 + 32 * q] : 0u;
+#pragma unroll
+          for (int q = 0; q < LW_ILP; q++) {
+            if (e0 + 32 * q >= cj) break;
+            sh_add16m(key, cnt, occ, lg, x2v[q], err);
+          }
         }
-#pragma unroll
-        for (int q = 0; q < LW_BATCH; q++)
-          if (wb + q * 32 + lane < tot) sh_add16m(key, cnt, occ, lg, x2v[q], err);
       }
     }
     __syncwarp();
@@ -445,40 +476,22 @@ __global__ void __launch_bounds__(LW_THREADS, 2) k_light(CArgs a0, const uint32_
       for (uint32_t k0 = 0; k0 < dp; k0 += 32) {
         const uint32_t i = k0 + lane;
         const bool v = i < dp;
-        uint32_t y = ky, c = kc, oy = koy, incl = kincl;
-        if (dp > 32) {
-          owner_nbr(a, base, i, v, y, c, oy);
-          incl = warp_incl_scan(c);
+        uint32_t y = ky, c = kc, oy = koy;
+        if (dp > 32) owner_nbr(a, base, i, v, y, c, oy);
+        const bool nar = PE && v && es_narrow(a, x1, a.off[y + 1] - a.off[y]);
+        uint32_t mine = 0;  // the sum over neighbour i's segment
+        for (uint32_t bm = __ballot_sync(FULL, c > 0); bm; bm &= bm - 1) {
+          const int j = __ffs(bm) - 1;
+          const uint32_t cj = __shfl_sync(FULL, c, j), oyj = __shfl_sync(FULL, oy, j);
+          const uint32_t sj = __shfl_sync(FULL, static_cast<uint32_t>(nar), j)
+                                  ? light_centre_walk<PE, true>(a, key, cnt, lg, oyj, cj, err)
+                                  : light_centre_walk<PE, false>(a, key, cnt, lg, oyj, cj, err);
+          if (lane == static_cast<uint32_t>(j)) mine = sj;
         }
-        const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        for (uint32_t wb = 0; wb < tot; wb += LW_BATCH * 32) {
-          uint32_t x2v[LW_BATCH], srcv[LW_BATCH], slv[LW_BATCH], dv[LW_BATCH];
-#pragma unroll
-          for (int q = 0; q < LW_BATCH; q++) {
-            const uint32_t wi = wb + q * 32 + lane;
-            warp_locate(incl, c, oy, wi < tot ? wi : tot - 1, srcv[q], slv[q]);
-            x2v[q] = wi < tot ? a.adj[slv[q]] : 0;
-          }
-#pragma unroll
-          for (int q = 0; q < LW_BATCH; q++)
-            dv[q] = wb + q * 32 + lane < tot ? sh_get16(key, cnt, lg, x2v[q], err) : 0;
-#pragma unroll
-          for (int q = 0; q < LW_BATCH; q++) {
-            unsigned long long t = dv[q] > 1 ? dv[q] - 1 : 0;
-            if (PE && t) atomicAdd(&a.es[slv[q]], t);
-            warp_run_add_rx(s_sum[w], srcv[q], t);
-          }
+        if (mine) {
+          if (PV) pv_add(s_hub, a, y, mine);
+          if (PE) atomicAdd(&a.es[base + i], static_cast<unsigned long long>(mine));
         }
-        __syncwarp();
-        if (v) {
-          unsigned long long sm = s_sum[w][lane];
-          if (sm) {
-            if (PV) pv_add(s_hub, a, y, sm);
-            if (PE) atomicAdd(&a.es[base + i], sm);
-            s_sum[w][lane] = 0;
-          }
-        }
-        __syncwarp();
       }
     }
     __syncwarp();
