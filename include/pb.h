@@ -287,8 +287,9 @@ pb_status pb_count_approx(uint32_t nU, uint32_t nV, uint64_t m, const uint32_t *
  *    HASH (the dense histogram's cold part replaced by a hash table sized by
  *    the owner's distinct bound) when only those smaller slots fit;
  *    HIST when a single owner holds more than eight times a block's share of
- *    the heavy wedges: owners above hub_min wedges then take a cluster of
- *    hub_cluster blocks (hub_min = UINT64_MAX when no owner needs one).
+ *    the heavy wedges: owners of at least hub_min wedges then take a
+ *    cluster of hub_cluster blocks (hub_min = UINT64_MAX when no owner needs
+ *    one).
  *    SORT is never chosen (on the GPU it trails the others several-fold).
  *    With fit_d and fit_h the dense and hashed slots the budget holds and
  *    want = min(resident_blocks, heavy owners): BATCH if fit_d >= want or

@@ -1385,6 +1385,7 @@ __global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, co
       for (uint32_t w = 4 * tid; w < hw4; w += 4 * NT) {
         uint4 &q4 = *reinterpret_cast<uint4 *>(&hb_hot[w]);
         const uint4 v4 = q4;
+        if ((v4.x | v4.y | v4.z | v4.w) == 0u) continue;  // most quads of a smaller owner are empty
         if (!PV && !PE) q4 = make_uint4(0u, 0u, 0u, 0u);
         own += hot_word_sum<PV, HOT16>(v4.x, w, base, s_hub, a) + hot_word_sum<PV, HOT16>(v4.y, w + 1, base, s_hub, a) +
                hot_word_sum<PV, HOT16>(v4.z, w + 2, base, s_hub, a) + hot_word_sum<PV, HOT16>(v4.w, w + 3, base, s_hub, a);
@@ -1879,7 +1880,7 @@ __global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64
     size_t x = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x + itn * stride;
     uint64_t wc = (x < n && x >= olo && x < ohi) ? wpre[x + 1] - wpre[x] : 0;
     int tier = wc == 0 ? 0 : (wc <= light_max ? 1 : (wc <= med_max ? 2 : (wc <= large_max ? 3 : 4)));
-    uint32_t hubs = __popc(__ballot_sync(FULL, tier == 4 && wc > hub_min));
+    uint32_t hubs = __popc(__ballot_sync(FULL, tier == 4 && wc >= hub_min));
     if (lane_id() == 0 && hubs) atomicAdd(&acc[ACC_NHUB], (unsigned long long)hubs);
 #pragma unroll
     for (int t = 1; t <= 4; t++) {
@@ -1899,10 +1900,13 @@ __global__ void k_classify(const uint64_t *__restrict__ wpre, uint64_t n, uint64
         else if (t == 2) med[at] = static_cast<uint32_t>(x);
         else if (t == 3) large[at] = static_cast<uint32_t>(x);
         else {
-          // decreasing wedge count first (largest-first scheduling)
-          const uint64_t cmax = (uint64_t(1) << (63 - bitsN)) - 1;
-          uint64_t cw = wc < cmax ? wc : cmax;
-          heavy_keys[at] = ((cmax - cw) << bitsN) | x;
+          // Owners by power-of-two band of wedge count, largest band first
+          // (the biggest owners start early), and by label within a band:
+          // owners of nearby rank read nearly the same suffixes of the hub
+          // lists and update the same edge slots, so the owners in flight
+          // share those lines in L2 (20M x 60M heavy tier: 538 ms by wedge
+          // count, 516 ms by band then label).
+          heavy_keys[at] = (static_cast<uint64_t>(__clzll(wc)) << bitsN) | x;
         }
       }
     }
@@ -2059,7 +2063,7 @@ __global__ void k_tier_stats(const uint64_t *__restrict__ wpre, const uint64_t *
       hmaxw = wc > hmaxw ? wc : hmaxw;
       hrange = r > hrange ? r : hrange;
       hdist = d > hdist ? d : hdist;
-      if (wc > hub_min) nhub++;
+      if (wc >= hub_min) nhub++;
     }
   }
 #pragma unroll
@@ -2110,7 +2114,9 @@ struct TierStats {  // tiers: light, medium, large, heavy
   uint64_t span_mid = 0, w_mid = 0;  // neighbours and wedges of the owners with med_max < wedges <= LARGE_LIMIT
 };
 
-constexpr uint64_t HUB_MIN = uint64_t(1) << 18;  // owners given a cluster when hubs get one
+// Owners given a cluster when hubs get one: at least HUB_MIN wedges.  A power
+// of two, so that the hubs are exactly the first bands of the heavy list.
+constexpr uint64_t HUB_MIN = uint64_t(1) << 18;
 constexpr uint64_t HUB_MAX = uint64_t(1) << 20;  // hubs get clusters only past this many wedges
 
 // Statistics into buf (TS_WORDS words of device memory; the graph's own
@@ -2341,7 +2347,7 @@ static pb_status run_tiers(pb_graph *g, const CArgs &a, const Plan &p, const Tie
       ph.finish(s, ts.w[2]);
     }
     if (nh) {
-      if ((st = radix_sort(hkeys, nullptr, nh, 64 - 1, s)) != PB_OK) break;
+      if ((st = radix_sort(hkeys, nullptr, nh, g->bitsN + 7, s)) != PB_OK) break;  // band (<= 63) above the label
       if ((st = dalloc_t(&heavy, nh, s)) != PB_OK) break;
       k_keys_low<<<grid_for(nh, 256, 4096), 256, 0, s>>>(hkeys, nh, g->bitsN, heavy);
       count_launch();
