@@ -1107,8 +1107,9 @@ __device__ __forceinline__ unsigned long long hot_word_sum(uint32_t v, uint32_t 
 // warp, rounded up to a power of two, at least SEG_CHUNK.
 constexpr uint32_t SEG_CHUNK = 256;
 // Adjacency loads per lane in flight in a segment walk (20M x 60M heavy tier:
-// 823 ms with one, 668 with two, 623 with four).
-constexpr int OWNER_ILP = 4;
+// 823 ms with one, 668 with two, 623 with four), per block size.
+constexpr int OWNER_ILP_HEAVY = 4, OWNER_ILP_LARGE = 4;
+__host__ __device__ constexpr int owner_ilp(int nt) { return nt >= 1024 ? OWNER_ILP_HEAVY : OWNER_ILP_LARGE; }
 
 // Chunk j of the staged neighbours: the neighbour k it belongs to (first k
 // with ck[k] > j), the end c of the chunk's range in that segment (its
@@ -1154,17 +1155,17 @@ __device__ __forceinline__ uint32_t next_unit(uint32_t *s_next, const uint32_t *
 // hot labels, so lanes walk independently; a cold label seen for the first
 // time is appended to the touched list with its own shared-memory add (cold
 // labels are a small share of the wedges).
-template <bool HOT16, bool HCOLD>
+template <bool HOT16, bool HCOLD, int ILP>
 __device__ __forceinline__ void owner_count_scan(const CArgs &a, uint32_t *hb_hot, const HeavySlots &h, uint32_t *A,
                                                  uint32_t *hkey, uint32_t *hval, uint32_t *T, uint32_t *s_nt, int lg,
                                                  uint32_t base, uint32_t oy, uint32_t e_lo, uint32_t c,
                                                  unsigned long long *err) {
-  for (uint32_t e0 = e_lo + lane_id(); e0 < c; e0 += 32 * OWNER_ILP) {
-    uint32_t x2v[OWNER_ILP];
+  for (uint32_t e0 = e_lo + lane_id(); e0 < c; e0 += 32 * ILP) {
+    uint32_t x2v[ILP];
 #pragma unroll
-    for (int q = 0; q < OWNER_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+    for (int q = 0; q < ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
 #pragma unroll
-    for (int q = 0; q < OWNER_ILP; q++) {
+    for (int q = 0; q < ILP; q++) {
       if (e0 + 32 * q >= c) break;
       const uint32_t x2 = x2v[q], r = x2 - base;
       if (r < h.hot) {
@@ -1192,7 +1193,7 @@ __device__ __forceinline__ void owner_count_scan(const CArgs &a, uint32_t *hb_ho
 // d - 1 added to the wedge's edge slot (32-bit partials when NARROW) and
 // summed for the centre.  Returns this lane's sum.  With 16-bit hot counts
 // every owner has fewer than 2^16 wedges, so a 32-bit sum cannot wrap.
-template <bool PE, bool HOT16, bool HCOLD, bool NARROW>
+template <bool PE, bool HOT16, bool HCOLD, bool NARROW, int ILP>
 __device__ __forceinline__ unsigned long long owner_centre_walk(const CArgs &a, const uint32_t *hb_hot,
                                                                 const HeavySlots &h, const uint32_t *A,
                                                                 const uint32_t *hkey, const uint32_t *hval, int lg,
@@ -1200,12 +1201,12 @@ __device__ __forceinline__ unsigned long long owner_centre_walk(const CArgs &a, 
                                                                 unsigned long long *err) {
   using S = typename std::conditional<HOT16, uint32_t, unsigned long long>::type;
   S sum = 0;
-  for (uint32_t e0 = e_lo + lane_id(); e0 < c; e0 += 32 * OWNER_ILP) {
-    uint32_t x2v[OWNER_ILP];
+  for (uint32_t e0 = e_lo + lane_id(); e0 < c; e0 += 32 * ILP) {
+    uint32_t x2v[ILP];
 #pragma unroll
-    for (int q = 0; q < OWNER_ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
+    for (int q = 0; q < ILP; q++) x2v[q] = e0 + 32 * q < c ? a.adj[oy + e0 + 32 * q] : 0u;
 #pragma unroll
-    for (int q = 0; q < OWNER_ILP; q++) {
+    for (int q = 0; q < ILP; q++) {
       const uint32_t e = e0 + 32 * q;
       if (e >= c) break;
       const uint32_t x2 = x2v[q], r = x2 - base;
@@ -1272,6 +1273,7 @@ __global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, co
   uint32_t *T = h.T + static_cast<size_t>(slot) * h.tcap;
   unsigned long long *err = &a0.acc[ACC_ERR];
   unsigned long long gacc = 0;
+  constexpr int ILP = owner_ilp(NT);
   const uint32_t hw = hot_words(h.hot, HOT16), hw4 = hw & ~3u;
   if (s_hub) hub_zero(s_hub);
   for (uint32_t t = tid; t < hw; t += NT) hb_hot[t] = 0;
@@ -1332,19 +1334,19 @@ __global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, co
         uint32_t c, oy, e_lo;
         if (next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo) == NT) break;
         if (scan) {
-          owner_count_scan<HOT16, HCOLD>(a, hb_hot, h, A, hkey, hval, T, &s_nt, lg, base, oy, e_lo, c, err);
+          owner_count_scan<HOT16, HCOLD, ILP>(a, hb_hot, h, A, hkey, hval, T, &s_nt, lg, base, oy, e_lo, c, err);
           continue;
         }
-        // OWNER_ILP adjacency loads per lane in flight before their counts
-        for (uint32_t e0 = e_lo; e0 < c; e0 += 32 * OWNER_ILP) {
-          uint32_t x2v[OWNER_ILP];
+        // ILP adjacency loads per lane in flight before their counts
+        for (uint32_t e0 = e_lo; e0 < c; e0 += 32 * ILP) {
+          uint32_t x2v[ILP];
 #pragma unroll
-          for (int q = 0; q < OWNER_ILP; q++) {
+          for (int q = 0; q < ILP; q++) {
             const uint32_t e = e0 + 32 * q + lane;
             x2v[q] = e < c ? a.adj[oy + e] : 0u;
           }
 #pragma unroll
-          for (int q = 0; q < OWNER_ILP; q++) {
+          for (int q = 0; q < ILP; q++) {
             if (e0 + 32 * q >= c) break;  // warp-uniform
             const bool act = e0 + 32 * q + lane < c;
             uint32_t tag = 0;
@@ -1445,8 +1447,8 @@ __global__ void __launch_bounds__(NT, owner_min_blocks(NT)) k_owner(CArgs a0, co
           const uint32_t k = next_unit<NT>(&s_next, s_ck, s_c, s_oy, split, units, ch, c, oy, e_lo);
           if (k == NT) break;
           const unsigned long long sum =
-              (PE && s_nar[k]) ? owner_centre_walk<PE, HOT16, HCOLD, true>(a, hb_hot, h, A, hkey, hval, lg, base, oy, e_lo, c, err)
-                               : owner_centre_walk<PE, HOT16, HCOLD, false>(a, hb_hot, h, A, hkey, hval, lg, base, oy, e_lo, c, err);
+              (PE && s_nar[k]) ? owner_centre_walk<PE, HOT16, HCOLD, true, ILP>(a, hb_hot, h, A, hkey, hval, lg, base, oy, e_lo, c, err)
+                               : owner_centre_walk<PE, HOT16, HCOLD, false, ILP>(a, hb_hot, h, A, hkey, hval, lg, base, oy, e_lo, c, err);
           if (lane == 0 && sum) {
             if (PV) pv_add(s_hub, a, s_y[k], sum);
             if (PE) atomicAdd(&a.es[xbase + s0 + k], sum);

@@ -110,7 +110,10 @@ pb_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, size_t n, cudaStrea
 // order of equal digits is the input order.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_IPT = 16;  // keys per thread
+// Keys per thread: eight, so that five blocks share an SM (the scatter is
+// latency-bound; 20M x 60M build + PREPROCESS 150.3 ms with sixteen keys and
+// three blocks per SM, 147.0 with twelve and four, 142.8 with eight and five).
+constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_BINS = 256;
 static_assert(RS_THREADS == RS_BINS, "one thread per digit in the scatter prefix");
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restri
 // digit-sorted order and written out in runs, so consecutive threads write
 // consecutive output positions.
 template <bool VALS>
-__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(
+__global__ void __launch_bounds__(RS_THREADS, 5) k_rs_scatter(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, size_t n, int shift, const uint32_t *__restrict__ offs,
     uint32_t ntiles) {
