@@ -588,6 +588,12 @@ def run_batched(args):
     return 0
 
 
+def noalloc_workload(workload: str) -> str:
+    """The allocation-free entry point's scratch takes sides of at most
+    16,777,184 vertices: the 20M x 60M default runs the 1M x 4M graph."""
+    return "cl2" if workload == "cl3" else workload
+
+
 def run_noalloc(args):
     """pb_count_noalloc, the allocation-free entry point, on caller-owned
     device buffers holding the library's own PREPROCESS output (global +
@@ -604,7 +610,7 @@ def run_noalloc(args):
     torch.cuda.set_device(0)
     pbuild.build()
     pb.load_library()
-    wl = "cl2" if args.workload == "cl3" else args.workload
+    wl = noalloc_workload(args.workload)
     g = synth.workload(WORKLOADS[wl]["idx"])
     G = pb.Graph.from_edges(g.nU, g.nV, g.u, g.v).rank("degree")
     W, n = G.wedges, g.nU + g.nV

@@ -90,3 +90,14 @@ def test_status_codes_raise_with_the_library_message():
             pb._check(code)
         assert ei.value.status == code
         assert pb.STATUS[code] in str(ei.value)
+
+
+def test_noalloc_mode_runs_a_graph_within_its_scratch(bench, monkeypatch):
+    """--mode noalloc times pb_count_noalloc; the 20M x 60M default has a side
+    beyond its fixed scratch, so the mode falls back to the 1M x 4M graph."""
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--mode", "noalloc"])
+    a = bench.parse()
+    assert a.mode == "noalloc" and bench.noalloc_workload(a.workload) == "cl2"
+    assert bench.noalloc_workload("cl3s") == "cl3s" and bench.noalloc_workload("er1") == "er1"
+    assert "cl2" in bench.WORKLOADS
